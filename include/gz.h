@@ -1,0 +1,266 @@
+/*
+ * gz.h - C ABI of libgz: exact vertex-induced pattern counting on one GB300
+ * (sm_103a), after GraphZero (Mawhirter et al., "GraphZero: Breaking Symmetry
+ * for Efficient Graph Mining", arXiv 1911.12877).
+ *
+ * Pipeline (Sec. 3): a pattern is planned on the host (schedule explorer,
+ * Algorithm 4; restrictions, Algorithm 1 reduced by Theorem 2; performance
+ * model, Sec. 5.4), the graph is optionally reindexed by decreasing degree on
+ * the GPU (orientation, Sec. 6), and the compiled nested loops run on the GPU
+ * with bounded set intersections and differences over sorted int32 neighbor
+ * lists, ending in one exact uint64 count.
+ *
+ * Conventions for every entry point:
+ *  - Every call returns a gz_status: GZ_OK (0) or a negative code. No call
+ *    aborts and no C++ exception crosses the ABI. gz_last_error() returns a
+ *    thread-local message for the last failing call of the calling thread.
+ *  - "stream" is a cudaStream_t (NULL = the legacy default stream). Calls that
+ *    return host results synchronise that stream before returning.
+ *  - Graphs: CSR with row_ptr int64[n+1] (row_ptr[0] = 0, row_ptr[n] = nnz,
+ *    non-decreasing) and col_idx int32[nnz]; each list strictly increasing
+ *    (sorted, no duplicates), no self-loops, symmetric (undirected graph).
+ *  - Patterns: k x k uint8 adjacency (row-major, symmetric, zero diagonal,
+ *    connected), 2 <= k <= GZ_MAX_K. Matching is vertex-induced (Sec. 2.1:
+ *    pattern edges are intersections, absent edges are differences).
+ *  - Objects are owned by the library and freed with their *_destroy call.
+ *  - Counts are exact uint64; overflow beyond 2^64 - 1 is not detected.
+ */
+#ifndef GZ_H
+#define GZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t gz_status;
+#define GZ_OK 0
+#define GZ_EINVAL (-1)       /* bad argument, malformed CSR or pattern */
+#define GZ_ENOMEM (-2)       /* device or host allocation failed */
+#define GZ_ECUDA (-3)        /* a CUDA runtime call failed */
+#define GZ_ETIMEOUT (-4)     /* a bounded wait ran out */
+#define GZ_EUNSUPPORTED (-5) /* e.g. no sm_100-family device */
+#define GZ_EOVERFLOW (-6)    /* a size does not fit the library's limits */
+#define GZ_EBUSY (-7)        /* resource in use (server full) */
+
+#define GZ_MAX_K 8
+
+typedef struct gz_graph gz_graph;   /* device CSR (+ oriented view), opaque */
+typedef struct gz_plan gz_plan;     /* compiled schedule, opaque */
+typedef struct gz_server gz_server; /* continuous-batching request loop, opaque */
+
+/* ------------------------------------------------------------------ graphs */
+
+#define GZ_VALIDATE 1u           /* check sortedness, range, self-loops on the GPU */
+#define GZ_VALIDATE_SYMMETRIC 2u /* also check u in N(v) <=> v in N(u) */
+
+/*
+ * Loads an undirected graph stored as sorted neighbor lists (Sec. 6: lists are
+ * sorted integer arrays scanned linearly).
+ *  row_ptr, col_idx: the CSR (layout above). device_ptrs = 0: host arrays,
+ *    copied to the device (the library owns the copy); device_ptrs = 1: device
+ *    arrays borrowed by the graph, which must outlive it and stay unchanged.
+ *  n >= 0 vertices, nnz >= 0 entries (2 x edges). flags: GZ_VALIDATE bits.
+ *  *out receives the graph. Errors: GZ_EINVAL (bad sizes or a CSR that fails
+ *  validation), GZ_ENOMEM, GZ_ECUDA. On error *out is NULL.
+ */
+gz_status gz_load_csr(const int64_t* row_ptr, const int32_t* col_idx, int64_t n, int64_t nnz,
+                      int device_ptrs, uint32_t flags, void* stream, gz_graph** out);
+
+/*
+ * Orientation (Sec. 6): reindexes vertices so a higher degree gets a smaller id
+ * (ties broken by the original id, ascending), relabels and re-sorts every
+ * list, and builds the out-list view N'(v) intersect [0, v) as a compact DAG
+ * CSR. The original view is kept; counts may use either (use_orientation).
+ * Idempotent. Errors: GZ_EINVAL (NULL graph), GZ_ENOMEM, GZ_ECUDA.
+ */
+gz_status gz_orient(gz_graph* g, void* stream);
+
+typedef struct {
+    int64_t n, nnz;
+    int64_t max_degree;
+    int64_t max_out_degree_original; /* max |N(v) intersect [0, v)|, original ids */
+    int64_t max_out_degree_oriented; /* same after reindexing; 0 if not oriented */
+    int32_t oriented;
+    int64_t device_bytes;            /* device memory held by the graph */
+} gz_graph_stats;
+
+gz_status gz_graph_info(const gz_graph* g, gz_graph_stats* out);
+
+/*
+ * Copies a view back to host memory: row_ptr int64[n+1], col int32[nnz] of the
+ * original (oriented = 0) or reindexed (oriented = 1) graph, and new_id
+ * int32[n] (old id -> new id; may be NULL; only for oriented = 1).
+ * Errors: GZ_EINVAL (not oriented when oriented = 1), GZ_ECUDA.
+ */
+gz_status gz_graph_export(const gz_graph* g, int oriented, int64_t* row_ptr, int32_t* col,
+                          int32_t* new_id, void* stream);
+
+void gz_graph_destroy(gz_graph* g);
+
+/* ---------------------------------------------------------------- patterns */
+
+/*
+ * Adjacency of a named pattern: edge, wedge, triangle, path4, star3, c4, paw
+ * (tailed triangle, Sec. 5.1), diamond, k4, c5, house, hourglass, chordal5
+ * (K5 minus an edge, "chordal cycle", Sec. 1), k5, k6, chordal6, k7, chordal7.
+ * adj must hold GZ_MAX_K * GZ_MAX_K bytes; the first k*k are written.
+ * Errors: GZ_EINVAL (unknown name).
+ */
+gz_status gz_pattern_named(const char* name, int* k, uint8_t* adj);
+
+/* ------------------------------------------------------------------- plans */
+
+#define GZ_PLAN_DEFAULT 0u
+
+/*
+ * Plans a pattern: Aut(P) by trying all k! permutations (Sec. 4.2); the
+ * distinct schedules by Algorithm 4 (Sec. 5.3); for each, the restrictions of
+ * Algorithm 1 reduced to one bound per loop by Theorem 2 and the cost of the
+ * Sec. 5.4 performance model; the cheapest schedule (first on ties) is
+ * compiled into the nested-loop program the kernels run.
+ * Errors: GZ_EINVAL (k out of range, not symmetric, self-loop, disconnected).
+ */
+gz_status gz_plan_create(int k, const uint8_t* adj, uint32_t flags, gz_plan** out);
+
+/* Same, with the schedule fixed to `order` (labels; must be valid, Sec. 2.1). */
+gz_status gz_plan_create_with_order(int k, const uint8_t* adj, const int32_t* order,
+                                    gz_plan** out);
+
+/*
+ * Plan summary: k; order[k] = schedule (labels); bound_parent[k] = for each
+ * schedule position i, the position z whose vertex bounds it from above
+ * (id(e_i) < id(e_z), Theorems 1 and 2) or -1; aut_size = |Aut(P)|; est_cost =
+ * the performance model's value. Any output pointer may be NULL.
+ */
+gz_status gz_plan_info(const gz_plan* p, int* k, int32_t* order, int32_t* bound_parent,
+                       uint64_t* aut_size, double* est_cost);
+
+/*
+ * Algorithm 4: writes up to cap distinct schedules (k labels each) in
+ * generation order to orders and their number to *count.
+ */
+gz_status gz_plan_schedules(int k, const uint8_t* adj, int32_t* orders, int cap, int* count);
+
+/*
+ * Text listing of the compiled nested-loop program (one line per item, NUL
+ * terminated, truncated to cap bytes): "unit dag=D", then per loop t its set
+ * operations "op level=t dst=B left_buf=B left_pos=P left_dag=D left_iter=I
+ * bound=P excl=M rights=pos:sub:dag,..." and per loop d >= 2 its candidates
+ * "cand d=.. buf=.. pos=.. bound=.. dag=.. excl=..", and "buf b dag=D" per
+ * scratch buffer. For inspection and tests; the kernels read the binary form.
+ */
+gz_status gz_plan_describe(const gz_plan* p, char* buf, int cap);
+
+void gz_plan_destroy(gz_plan* p);
+
+/* ---------------------------------------------------------------- counting */
+
+/*
+ * Counts the instances of the plan's pattern in the graph (Sec. 4: each
+ * instance is found exactly once under the restrictions, Theorem 1), on the
+ * original ids (use_orientation = 0) or the reindexed graph (1; requires
+ * gz_orient first). The graph stays on the device; *out_count (host) receives
+ * the exact count. Scratch is allocated by the library and reused.
+ * Errors: GZ_EINVAL, GZ_ENOMEM, GZ_ECUDA.
+ */
+gz_status gz_count(const gz_plan* p, const gz_graph* g, int use_orientation, void* stream,
+                   uint64_t* out_count);
+
+typedef struct {
+    int use_orientation;
+    int64_t root_lo, root_hi; /* only roots (first scheduled vertex) in [lo, hi); hi < 0 = n */
+    int block_warps;          /* warps per CTA, 0 = default */
+    int chunk;                /* work units per queue pop, 0 = default or autotuned */
+} gz_count_opts;
+
+/*
+ * gz_count with options. Roots are vertex ids in the view being counted
+ * (reindexed ids when use_orientation = 1). The sum over a partition of the
+ * root range equals the full count. Errors as gz_count.
+ */
+gz_status gz_count_ex(const gz_plan* p, const gz_graph* g, const gz_count_opts* opts,
+                      void* stream, uint64_t* out_count);
+
+/*
+ * Device scratch gz_count needs for this plan and graph (bytes), so callers can
+ * budget memory before admitting a query.
+ */
+gz_status gz_scratch_bytes(const gz_plan* p, const gz_graph* g, int use_orientation,
+                           uint64_t* bytes);
+
+/*
+ * Batched counting: nq independent (plan, graph, use_orientation[i]) queries in
+ * one persistent launch over a device work queue (no paper counterpart; the
+ * merged multi-pattern program of Sec. 3 is the closest). out_counts[nq] (host)
+ * receives each query's exact count, identical to gz_count of that query.
+ * Errors: GZ_EINVAL, GZ_ENOMEM, GZ_ECUDA.
+ */
+gz_status gz_count_batch(const gz_plan* const* plans, const gz_graph* const* graphs,
+                         const int* use_orientation, int nq, void* stream,
+                         uint64_t* out_counts);
+
+/*
+ * Autotuner: times candidate launch shapes (warps per CTA, units per queue pop)
+ * for this (plan, graph) on the device and caches the fastest; later counts of
+ * the same pair use it. Writes the choice to *block_warps and *chunk if not NULL.
+ */
+gz_status gz_autotune(const gz_plan* p, const gz_graph* g, int use_orientation, void* stream,
+                      int* block_warps, int* chunk);
+
+/* --------------------------------------------------------------- serving */
+
+typedef struct {
+    int max_inflight_launches; /* concurrent batched launches (streams), >= 1 */
+    int max_batch;             /* queries per launch */
+    uint64_t scratch_budget;   /* device bytes for in-flight scratch, 0 = 4 GiB */
+} gz_server_opts;
+
+/*
+ * Continuous-batching request loop over device-resident graphs. Requests are
+ * admitted as launch slots and scratch memory free up, batched with whatever
+ * else is waiting, and run on separate streams so their work overlaps.
+ */
+gz_status gz_server_create(const gz_server_opts* opts, gz_server** out);
+
+/* Submits one query; *ticket identifies it. Errors: GZ_EINVAL, GZ_EBUSY. */
+gz_status gz_server_submit(gz_server* s, const gz_plan* p, const gz_graph* g,
+                           int use_orientation, int64_t* ticket);
+
+/*
+ * Waits up to timeout_ms (< 0: forever) for ticket; on completion writes the
+ * count and the latency from submission to completion in nanoseconds.
+ * Errors: GZ_ETIMEOUT (not done yet), GZ_EINVAL (unknown ticket).
+ */
+gz_status gz_server_wait(gz_server* s, int64_t ticket, int64_t timeout_ms, uint64_t* count,
+                         int64_t* latency_ns);
+
+/*
+ * Replays a request trace in real time: request i (plan_idx[i] into plans,
+ * graph_idx[i] into graphs) is submitted at arrival_ns[i] after the call
+ * starts. Fills counts[i] and latency_ns[i] (arrival to completion).
+ * fifo = 1 runs the plain baseline instead: one query per launch, in arrival
+ * order, one at a time. stats_out (optional, 4 values): achieved requests/s,
+ * max queue depth, launches, wall seconds.
+ */
+gz_status gz_server_replay(gz_server* s, const gz_plan* const* plans,
+                           const gz_graph* const* graphs, const int* use_orientation,
+                           int64_t nreq, const int64_t* arrival_ns, const int32_t* plan_idx,
+                           const int32_t* graph_idx, int fifo, uint64_t* counts,
+                           int64_t* latency_ns, double* stats_out);
+
+void gz_server_destroy(gz_server* s);
+
+/* ------------------------------------------------------------------ misc */
+
+const char* gz_last_error(void);
+
+/* Library version string. */
+const char* gz_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GZ_H */

@@ -1,0 +1,530 @@
+// gz_api.cpp - the C ABI of libgz (declared in include/gz.h): argument checks,
+// ownership, device memory, launch configuration and the autotuner cache.
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "gz_internal.h"
+
+namespace gz {
+
+namespace {
+thread_local char g_err[512] = "";
+}
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+gz_status cuda_fail(cudaError_t e, const char* what) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    cudaGetLastError();  // clear a non-sticky error
+    return e == cudaErrorMemoryAllocation ? GZ_ENOMEM : GZ_ECUDA;
+}
+
+gz_status max_degree(const int64_t* rp, int64_t n, int64_t* out, cudaStream_t s);
+gz_status validate_csr(const int64_t* rp, const int32_t* col, int64_t n, int64_t nnz,
+                       bool symmetric, cudaStream_t s);
+gz_status make_plan(int k, const uint8_t* adj, const int32_t* forced_order, gz_plan** out);
+gz_status list_schedules(int k, const uint8_t* adj, int32_t* orders, int cap, int* count);
+
+// ------------------------------------------------------------ scratch arena
+
+// One growable device scratch region for the synchronous counting calls.
+struct Arena {
+    std::mutex mu;
+    void* ptr = nullptr;
+    uint64_t bytes = 0;
+    int device = -1;
+};
+Arena& arena() {
+    static Arena a;
+    return a;
+}
+
+gz_status arena_reserve(Arena& a, uint64_t bytes) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (a.ptr && a.bytes >= bytes && a.device == dev) return GZ_OK;
+    if (a.ptr) {
+        cudaDeviceSynchronize();
+        cudaFree(a.ptr);
+        a.ptr = nullptr;
+        a.bytes = 0;
+    }
+    uint64_t want = bytes < (64ull << 20) ? (64ull << 20) : bytes;
+    cudaError_t e = cudaMalloc(&a.ptr, want);
+    if (e != cudaSuccess) {
+        a.ptr = nullptr;
+        return cuda_fail(e, "scratch cudaMalloc");
+    }
+    a.bytes = want;
+    a.device = dev;
+    return GZ_OK;
+}
+
+// ------------------------------------------------------------ autotune cache
+
+struct TuneKey {
+    const gz_plan* p;
+    const gz_graph* g;
+    int ori;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(p, g, ori) < std::tie(o.p, o.g, o.ori);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, LaunchCfg>& tune_cache() {
+    static std::map<TuneKey, LaunchCfg> m;
+    return m;
+}
+
+void forget_graph(const gz_graph* g) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto& m = tune_cache();
+    for (auto it = m.begin(); it != m.end();) it = it->first.g == g ? m.erase(it) : std::next(it);
+}
+void forget_plan(const gz_plan* p) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto& m = tune_cache();
+    for (auto it = m.begin(); it != m.end();) it = it->first.p == p ? m.erase(it) : std::next(it);
+}
+
+// ------------------------------------------------------------ query preparation
+
+// Picks the view, builds the out-list / unit arrays it needs, and turns a root
+// range into a unit (edge) range.
+gz_status prepare_query(const gz_plan* p, const gz_graph* gc, int use_orientation, int64_t root_lo,
+                        int64_t root_hi, cudaStream_t s, Query& q) {
+    gz_graph* g = const_cast<gz_graph*>(gc);
+    if (use_orientation && !g->oriented) {
+        set_error("count: use_orientation = 1 needs gz_orient first");
+        return GZ_EINVAL;
+    }
+    GzView* v = use_orientation ? &g->ori : &g->orig;
+    gz_status st = build_dag(g, v, s);
+    if (st != GZ_OK) return st;
+    if (!p->prog.unit_dag) {
+        st = build_src(g, v, s);
+        if (st != GZ_OK) return st;
+    }
+    q.prog = &p->prog;
+    q.g = g;
+    q.view = v;
+    if (root_lo < 0) root_lo = 0;
+    if (root_hi < 0 || root_hi > g->n) root_hi = g->n;
+    if (root_lo >= root_hi) {
+        q.unit_lo = q.unit_hi = 0;
+        return GZ_OK;
+    }
+    const int64_t* urp = p->prog.unit_dag ? v->dag_rp : v->rp;
+    if (root_lo == 0 && root_hi == g->n) {
+        q.unit_lo = 0;
+        q.unit_hi = p->prog.unit_dag ? v->dag_nnz : g->nnz;
+        return GZ_OK;
+    }
+    int64_t ends[2];
+    cudaError_t e = cudaMemcpyAsync(&ends[0], urp + root_lo, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[1], urp + root_hi, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "count: unit range");
+    q.unit_lo = ends[0];
+    q.unit_hi = ends[1];
+    return GZ_OK;
+}
+
+LaunchCfg default_cfg() {
+    LaunchCfg c;
+    c.block_warps = 8;
+    c.chunk = 4;
+    return c;
+}
+
+// Runs nq queries in one launch and copies their counts to the host.
+gz_status run_queries(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream_t s,
+                      uint64_t* out_counts) {
+    uint64_t words = 0;
+    for (int i = 0; i < nq; ++i)
+        words = std::max(words, scratch_words_per_warp(*qs[i].prog, *qs[i].g, *qs[i].view));
+    const uint64_t need = (uint64_t)resident_warps(cfg) * words * sizeof(int32_t);
+    Arena& a = arena();
+    std::lock_guard<std::mutex> lk(a.mu);
+    gz_status st = arena_reserve(a, need);
+    if (st != GZ_OK) return st;
+    unsigned long long* d = nullptr;
+    cudaError_t e = cudaMallocAsync(&d, sizeof(unsigned long long) * (nq + 1), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync counts");
+    int* d_status = reinterpret_cast<int*>(d + nq);
+    e = cudaMemsetAsync(d, 0, sizeof(unsigned long long) * (nq + 1), s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(d, s);
+        return cuda_fail(e, "memset counts");
+    }
+    st = count_launch(qs, nq, cfg, s, d, a.ptr, a.bytes, d_status);
+    std::vector<unsigned long long> h(nq + 1);
+    if (st == GZ_OK) {
+        e = cudaMemcpyAsync(h.data(), d, sizeof(unsigned long long) * (nq + 1), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_fail(e, "count");
+    }
+    cudaFreeAsync(d, s);
+    if (st != GZ_OK) return st;
+    if (*reinterpret_cast<int*>(&h[nq]) != 0) {
+        set_error("count: a scratch buffer overflowed (planner capacity bug)");
+        return GZ_EOVERFLOW;
+    }
+    for (int i = 0; i < nq; ++i) out_counts[i] = h[i];
+    return GZ_OK;
+}
+
+bool check_graph(const gz_graph* g, const char* who) {
+    if (!g) {
+        set_error("%s: graph is NULL", who);
+        return false;
+    }
+    return true;
+}
+
+}  // namespace gz
+
+using namespace gz;
+
+extern "C" {
+
+const char* gz_last_error(void) { return gz::g_err; }
+const char* gz_version(void) { return "gz-gb300 0.1 (sm_103a)"; }
+
+gz_status gz_load_csr(const int64_t* row_ptr, const int32_t* col_idx, int64_t n, int64_t nnz,
+                      int device_ptrs, uint32_t flags, void* stream, gz_graph** out) {
+    if (!out) { set_error("gz_load_csr: out is NULL"); return GZ_EINVAL; }
+    *out = nullptr;
+    if (n < 0 || nnz < 0 || !row_ptr || (nnz > 0 && !col_idx)) {
+        set_error("gz_load_csr: bad sizes or NULL arrays (n = %lld, nnz = %lld)", (long long)n, (long long)nnz);
+        return GZ_EINVAL;
+    }
+    if (n > (int64_t)INT32_MAX - 1 || nnz > ((int64_t)1 << 40)) {
+        set_error("gz_load_csr: graph too large for int32 ids");
+        return GZ_EOVERFLOW;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    gz_graph* g = new (std::nothrow) gz_graph;
+    if (!g) { set_error("gz_load_csr: out of host memory"); return GZ_ENOMEM; }
+    g->n = n;
+    g->nnz = nnz;
+    cudaGetDevice(&g->device);
+    cudaError_t e = cudaSuccess;
+    if (device_ptrs) {
+        g->orig.rp = const_cast<int64_t*>(row_ptr);
+        g->orig.col = const_cast<int32_t*>(col_idx);
+        g->orig.owned_csr = false;
+    } else {
+        e = cudaMalloc(&g->orig.rp, sizeof(int64_t) * (n + 1));
+        if (e == cudaSuccess) e = cudaMalloc(&g->orig.col, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g->orig.rp, row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && nnz > 0)
+            e = cudaMemcpyAsync(g->orig.col, col_idx, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            gz_status st = cuda_fail(e, "gz_load_csr: copy");
+            gz_graph_destroy(g);
+            return st;
+        }
+    }
+    gz_status st = GZ_OK;
+    if (flags & (GZ_VALIDATE | GZ_VALIDATE_SYMMETRIC))
+        st = validate_csr(g->orig.rp, g->orig.col, n, nnz, (flags & GZ_VALIDATE_SYMMETRIC) != 0, s);
+    if (st == GZ_OK) st = max_degree(g->orig.rp, n, &g->max_deg, s);
+    if (st != GZ_OK) {
+        gz_graph_destroy(g);
+        return st;
+    }
+    *out = g;
+    return GZ_OK;
+}
+
+gz_status gz_orient(gz_graph* g, void* stream) {
+    if (!check_graph(g, "gz_orient")) return GZ_EINVAL;
+    return gz::orient(g, (cudaStream_t)stream);
+}
+
+gz_status gz_graph_info(const gz_graph* g, gz_graph_stats* out) {
+    if (!check_graph(g, "gz_graph_info") || !out) return GZ_EINVAL;
+    gz_graph* gg = const_cast<gz_graph*>(g);
+    gz_status st = build_dag(gg, &gg->orig, 0);
+    if (st != GZ_OK) return st;
+    cudaStreamSynchronize(0);
+    memset(out, 0, sizeof(*out));
+    out->n = g->n;
+    out->nnz = g->nnz;
+    out->max_degree = g->max_deg;
+    out->max_out_degree_original = g->orig.max_out;
+    out->max_out_degree_oriented = g->oriented ? g->ori.max_out : 0;
+    out->oriented = g->oriented ? 1 : 0;
+    int64_t b = 0;
+    auto view_bytes = [&](const GzView& v, bool csr) {
+        int64_t x = 0;
+        if (csr && v.rp) x += 8 * (g->n + 1) + 4 * g->nnz;
+        if (v.has_dag) x += 8 * (g->n + 1) + 8 * v.dag_nnz;
+        if (v.src) x += 4 * g->nnz;
+        return x;
+    };
+    b += view_bytes(g->orig, g->orig.owned_csr);
+    b += view_bytes(g->ori, true);
+    if (g->new_id) b += 4 * g->n;
+    out->device_bytes = b;
+    return GZ_OK;
+}
+
+gz_status gz_graph_export(const gz_graph* g, int oriented, int64_t* row_ptr, int32_t* col,
+                          int32_t* new_id, void* stream) {
+    if (!check_graph(g, "gz_graph_export") || !row_ptr || (g->nnz > 0 && !col)) return GZ_EINVAL;
+    if (oriented && !g->oriented) {
+        set_error("gz_graph_export: graph not oriented");
+        return GZ_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const GzView& v = oriented ? g->ori : g->orig;
+    cudaError_t e = cudaMemcpyAsync(row_ptr, v.rp, sizeof(int64_t) * (g->n + 1), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && g->nnz > 0)
+        e = cudaMemcpyAsync(col, v.col, sizeof(int32_t) * g->nnz, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && oriented && new_id && g->n > 0)
+        e = cudaMemcpyAsync(new_id, g->new_id, sizeof(int32_t) * g->n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "gz_graph_export");
+    return GZ_OK;
+}
+
+void gz_graph_destroy(gz_graph* g) {
+    if (!g) return;
+    forget_graph(g);
+    auto free_view = [](GzView& v, bool csr) {
+        if (csr) { cudaFree(v.rp); cudaFree(v.col); }
+        cudaFree(v.dag_rp); cudaFree(v.dag_col); cudaFree(v.dag_src); cudaFree(v.src);
+    };
+    cudaDeviceSynchronize();
+    free_view(g->orig, g->orig.owned_csr);
+    free_view(g->ori, true);
+    cudaFree(g->new_id);
+    delete g;
+}
+
+gz_status gz_pattern_named(const char* name, int* k, uint8_t* adj) {
+    if (!name || !k || !adj) { set_error("gz_pattern_named: NULL argument"); return GZ_EINVAL; }
+    struct E { int a, b; };
+    std::vector<E> edges;
+    int kk = 0;
+    auto clique = [&](int n) { kk = n; for (int i = 0; i < n; ++i) for (int j = i + 1; j < n; ++j) edges.push_back({i, j}); };
+    auto chordal = [&](int n) { clique(n); edges.erase(std::remove_if(edges.begin(), edges.end(), [&](E e) { return e.a == n - 2 && e.b == n - 1; }), edges.end()); };
+    auto cyc = [&](int n) { kk = n; for (int i = 0; i < n; ++i) edges.push_back({i, (i + 1) % n}); };
+    std::string s(name);
+    if (s == "edge") { kk = 2; edges = {{0, 1}}; }
+    else if (s == "wedge") { kk = 3; edges = {{0, 1}, {0, 2}}; }
+    else if (s == "triangle" || s == "k3") clique(3);
+    else if (s == "path4") { kk = 4; edges = {{0, 1}, {1, 2}, {2, 3}}; }
+    else if (s == "star3") { kk = 4; edges = {{0, 1}, {0, 2}, {0, 3}}; }
+    else if (s == "c4" || s == "rectangle") cyc(4);
+    else if (s == "paw" || s == "tailed_triangle") { kk = 4; edges = {{0, 1}, {1, 2}, {0, 2}, {2, 3}}; }
+    else if (s == "diamond" || s == "chordal4") chordal(4);
+    else if (s == "k4") clique(4);
+    else if (s == "c5" || s == "pentagon") cyc(5);
+    else if (s == "house") { cyc(4); edges.push_back({0, 4}); edges.push_back({1, 4}); kk = 5; }
+    else if (s == "hourglass") { kk = 5; edges = {{0, 1}, {0, 2}, {1, 2}, {0, 3}, {0, 4}, {3, 4}}; }
+    else if (s == "chordal5") chordal(5);
+    else if (s == "k5") clique(5);
+    else if (s == "k6") clique(6);
+    else if (s == "chordal6") chordal(6);
+    else if (s == "k7") clique(7);
+    else if (s == "chordal7") chordal(7);
+    else {
+        set_error("gz_pattern_named: unknown pattern '%s'", name);
+        return GZ_EINVAL;
+    }
+    *k = kk;
+    memset(adj, 0, (size_t)kk * kk);
+    for (const E& e : edges) adj[e.a * kk + e.b] = adj[e.b * kk + e.a] = 1;
+    return GZ_OK;
+}
+
+gz_status gz_plan_create(int k, const uint8_t* adj, uint32_t flags, gz_plan** out) {
+    (void)flags;
+    return make_plan(k, adj, nullptr, out);
+}
+
+gz_status gz_plan_create_with_order(int k, const uint8_t* adj, const int32_t* order, gz_plan** out) {
+    if (!order) { set_error("gz_plan_create_with_order: order is NULL"); return GZ_EINVAL; }
+    return make_plan(k, adj, order, out);
+}
+
+gz_status gz_plan_info(const gz_plan* p, int* k, int32_t* order, int32_t* bound_parent,
+                       uint64_t* aut_size, double* est_cost) {
+    if (!p) { set_error("gz_plan_info: plan is NULL"); return GZ_EINVAL; }
+    if (k) *k = p->k;
+    if (order) memcpy(order, p->order, sizeof(int32_t) * p->k);
+    if (bound_parent) memcpy(bound_parent, p->bp, sizeof(int32_t) * p->k);
+    if (aut_size) *aut_size = p->aut_size;
+    if (est_cost) *est_cost = p->est_cost;
+    return GZ_OK;
+}
+
+gz_status gz_plan_schedules(int k, const uint8_t* adj, int32_t* orders, int cap, int* count) {
+    return list_schedules(k, adj, orders, cap, count);
+}
+
+gz_status gz_plan_describe(const gz_plan* p, char* buf, int cap) {
+    if (!p || !buf || cap <= 0) { set_error("gz_plan_describe: bad arguments"); return GZ_EINVAL; }
+    const GzProg& g = p->prog;
+    std::string s = "unit dag=" + std::to_string(g.unit_dag) + "\n";
+    for (int i = 0; i < g.nops; ++i) {
+        const GzOp& o = g.ops[i];
+        char line[256];
+        snprintf(line, sizeof(line),
+                 "op level=%d dst=%d left_buf=%d left_pos=%d left_dag=%d left_iter=%d bound=%d excl=%d rights=",
+                 o.level, o.dst, o.left_buf, o.left_pos, o.left_dag, o.left_iter, o.bound_pos, o.excl_mask);
+        s += line;
+        for (int r = 0; r < o.nright; ++r) {
+            snprintf(line, sizeof(line), "%s%d:%d:%d", r ? "," : "", o.right_pos[r], o.right_sub[r], o.right_dag[r]);
+            s += line;
+        }
+        s += "\n";
+    }
+    for (int d = 2; d <= g.k - 2; ++d) {
+        char line[160];
+        snprintf(line, sizeof(line), "cand d=%d buf=%d pos=%d bound=%d dag=%d excl=%d\n", d, g.cand_buf[d],
+                 g.cand_pos[d], g.cand_bound[d], g.cand_dag[d], g.cand_excl[d]);
+        s += line;
+    }
+    for (int b = 0; b < g.nbuf; ++b) s += "buf " + std::to_string(b) + " dag=" + std::to_string(g.buf_dag[b]) + "\n";
+    snprintf(buf, (size_t)cap, "%s", s.c_str());
+    return GZ_OK;
+}
+
+void gz_plan_destroy(gz_plan* p) {
+    if (!p) return;
+    forget_plan(p);
+    delete p;
+}
+
+gz_status gz_count_ex(const gz_plan* p, const gz_graph* g, const gz_count_opts* opts, void* stream,
+                      uint64_t* out_count) {
+    if (!p || !check_graph(g, "gz_count") || !out_count) {
+        if (!p) set_error("gz_count: plan is NULL");
+        if (!out_count) set_error("gz_count: out_count is NULL");
+        return GZ_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    gz_count_opts o{};
+    o.root_hi = -1;
+    if (opts) o = *opts;
+    Query q{};
+    gz_status st = prepare_query(p, g, o.use_orientation, o.root_lo, o.root_hi, s, q);
+    if (st != GZ_OK) return st;
+    LaunchCfg cfg = default_cfg();
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = tune_cache().find(TuneKey{p, g, o.use_orientation ? 1 : 0});
+        if (it != tune_cache().end()) cfg = it->second;
+    }
+    if (o.block_warps > 0) cfg.block_warps = std::min(16, o.block_warps);
+    if (o.chunk > 0) cfg.chunk = o.chunk;
+    *out_count = 0;
+    if (q.unit_hi <= q.unit_lo) return GZ_OK;
+    return run_queries(&q, 1, cfg, s, out_count);
+}
+
+gz_status gz_count(const gz_plan* p, const gz_graph* g, int use_orientation, void* stream,
+                   uint64_t* out_count) {
+    gz_count_opts o{};
+    o.use_orientation = use_orientation;
+    o.root_hi = -1;
+    return gz_count_ex(p, g, &o, stream, out_count);
+}
+
+gz_status gz_scratch_bytes(const gz_plan* p, const gz_graph* g, int use_orientation, uint64_t* bytes) {
+    if (!p || !check_graph(g, "gz_scratch_bytes") || !bytes) return GZ_EINVAL;
+    if (use_orientation && !g->oriented) { set_error("gz_scratch_bytes: graph not oriented"); return GZ_EINVAL; }
+    gz_graph* gg = const_cast<gz_graph*>(g);
+    GzView* v = use_orientation ? &gg->ori : &gg->orig;
+    gz_status st = build_dag(gg, v, 0);
+    if (st != GZ_OK) return st;
+    *bytes = (uint64_t)resident_warps(default_cfg()) * scratch_words_per_warp(p->prog, *g, *v) * 4;
+    return GZ_OK;
+}
+
+gz_status gz_count_batch(const gz_plan* const* plans, const gz_graph* const* graphs,
+                         const int* use_orientation, int nq, void* stream, uint64_t* out_counts) {
+    if (nq < 0 || (nq > 0 && (!plans || !graphs || !out_counts))) {
+        set_error("gz_count_batch: bad arguments");
+        return GZ_EINVAL;
+    }
+    if (nq == 0) return GZ_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<Query> qs(nq);
+    for (int i = 0; i < nq; ++i) {
+        if (!plans[i] || !graphs[i]) { set_error("gz_count_batch: NULL plan or graph at %d", i); return GZ_EINVAL; }
+        gz_status st = prepare_query(plans[i], graphs[i], use_orientation ? use_orientation[i] : 0,
+                                     0, -1, s, qs[i]);
+        if (st != GZ_OK) return st;
+    }
+    // heaviest queries first (largest unit count x depth), so their tails start early
+    std::vector<int> idx(nq);
+    for (int i = 0; i < nq; ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+        double wa = (double)(qs[a].unit_hi - qs[a].unit_lo) * qs[a].prog->k;
+        double wb = (double)(qs[b].unit_hi - qs[b].unit_lo) * qs[b].prog->k;
+        return wa > wb;
+    });
+    std::vector<Query> sorted(nq);
+    for (int i = 0; i < nq; ++i) sorted[i] = qs[idx[i]];
+    std::vector<uint64_t> res(nq, 0);
+    LaunchCfg cfg = default_cfg();
+    gz_status st = run_queries(sorted.data(), nq, cfg, s, res.data());
+    if (st != GZ_OK) return st;
+    for (int i = 0; i < nq; ++i) out_counts[idx[i]] = res[i];
+    return GZ_OK;
+}
+
+gz_status gz_autotune(const gz_plan* p, const gz_graph* g, int use_orientation, void* stream,
+                      int* block_warps, int* chunk) {
+    if (!p || !check_graph(g, "gz_autotune")) return GZ_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    Query q{};
+    gz_status st = prepare_query(p, g, use_orientation, 0, -1, s, q);
+    if (st != GZ_OK) return st;
+    const int bw_c[] = {4, 8, 16};
+    const int ch_c[] = {1, 4, 16};
+    LaunchCfg best = default_cfg();
+    double best_t = 1e300;
+    if (q.unit_hi > q.unit_lo) {
+        for (int bw : bw_c)
+            for (int ch : ch_c) {
+                LaunchCfg c;
+                c.block_warps = bw;
+                c.chunk = ch;
+                uint64_t cnt = 0;
+                auto t0 = std::chrono::steady_clock::now();
+                st = run_queries(&q, 1, c, s, &cnt);
+                double t = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+                if (st != GZ_OK) return st;
+                if (t < best_t) { best_t = t; best = c; }
+            }
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_cache()[TuneKey{p, g, use_orientation ? 1 : 0}] = best;
+    }
+    if (block_warps) *block_warps = best.block_warps;
+    if (chunk) *chunk = best.chunk;
+    return GZ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,382 @@
+// gz_count.cu - the enumeration kernels: the compiled nested loops of GraphZero
+// (Sec. 4) run by one warp per work unit, with bounded set operations on sorted
+// int32 neighbor lists (Sec. 6) and an exact uint64 reduction.
+//
+// Execution model
+//  - A work unit is one edge (e0, e1) of the level-1 candidate lists: an
+//    out-list entry (e1 < e0) when loop 1 is bounded by loop 0, else a full
+//    adjacency entry. Units are popped from a device counter in chunks by a
+//    persistent grid (resident CTAs on every SM), which splits skewed roots at
+//    edge granularity.
+//  - A warp binds e0, e1, runs loop 1's operations, then walks loops 2..k-2 as
+//    an explicit DFS. Each set operation streams its left list 32 elements at a
+//    time (coalesced), probes every right list by binary search, and either
+//    compacts the survivors into the warp's scratch buffer (ballot + popc) or,
+//    on the last loop, only counts them.
+//  - Counts are per-lane uint64, reduced by warp shuffles and added to the
+//    query's slot with one atomic per warp per query. Integer adds are exact and
+//    order-independent, so the result is bit-exact whatever the schedule.
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "gz_internal.h"
+
+namespace gz {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Per-query descriptor in device memory.
+struct KQ {
+    GzProg prog;
+    const int64_t* rp;
+    const int32_t* col;
+    const int64_t* drp;
+    const int32_t* dcol;
+    const int32_t* usrc;   // unit CSR: source of each unit edge
+    const int32_t* ucol;   // unit CSR: target of each unit edge
+    const int64_t* urp;    // unit CSR rows (position of e1 within e0's list)
+    int64_t unit_lo;       // first unit (edge index) of this query
+    int64_t unit_begin;    // offset of this query in the launch's unit space
+    int64_t unit_count;
+    int64_t buf_off[GZ_MAXBUF];
+    int64_t buf_cap[GZ_MAXBUF];
+};
+
+// Number of elements of sorted L[0, n) that are < beta (warp-cooperative
+// 32-ary search; every lane returns the same value).
+__device__ __forceinline__ int64_t warp_lower_bound(const int32_t* __restrict__ L, int64_t n,
+                                                    int32_t beta, int lane) {
+    int64_t lo = 0, hi = n;
+    while (hi - lo > 32) {
+        int64_t step = (hi - lo + 31) >> 5;
+        int64_t p = lo + (int64_t)lane * step;
+        bool less = p < hi && __ldg(L + p) < beta;
+        int c = __popc(__ballot_sync(kFull, less));
+        if (c == 0) return lo;
+        int64_t nlo = lo + (int64_t)(c - 1) * step + 1;
+        int64_t nhi = lo + (int64_t)c * step;
+        lo = nlo;
+        hi = nhi < hi ? nhi : hi;
+    }
+    int64_t p = lo + lane;
+    bool less = p < hi && __ldg(L + p) < beta;
+    return lo + __popc(__ballot_sync(kFull, less));
+}
+
+// Same, for scratch buffers written earlier by this warp (no read-only path).
+__device__ __forceinline__ int64_t warp_lower_bound_rw(const int32_t* L, int64_t n, int32_t beta,
+                                                       int lane) {
+    int64_t lo = 0, hi = n;
+    while (hi - lo > 32) {
+        int64_t step = (hi - lo + 31) >> 5;
+        int64_t p = lo + (int64_t)lane * step;
+        bool less = p < hi && L[p] < beta;
+        int c = __popc(__ballot_sync(kFull, less));
+        if (c == 0) return lo;
+        int64_t nlo = lo + (int64_t)(c - 1) * step + 1;
+        int64_t nhi = lo + (int64_t)c * step;
+        lo = nlo;
+        hi = nhi < hi ? nhi : hi;
+    }
+    int64_t p = lo + lane;
+    bool less = p < hi && L[p] < beta;
+    return lo + __popc(__ballot_sync(kFull, less));
+}
+
+// Is x in sorted R[0, n)? (per-lane binary search)
+__device__ __forceinline__ bool contains(const int32_t* __restrict__ R, int n, int32_t x) {
+    int lo = 0, len = n;
+    while (len > 0) {
+        int half = len >> 1;
+        int32_t v = __ldg(R + lo + half);
+        if (v < x) { lo += half + 1; len -= half + 1; }
+        else len = half;
+    }
+    return lo < n && __ldg(R + lo) == x;
+}
+
+struct ListRef {
+    const int32_t* p;
+    int64_t n;
+};
+
+// N(v), or its out-list part when dag != 0.
+__device__ __forceinline__ ListRef adj_list(const KQ& q, int32_t v, int dag) {
+    ListRef r;
+    if (dag) {
+        int64_t b = q.drp[v];
+        r.p = q.dcol + b;
+        r.n = q.drp[v + 1] - b;
+    } else {
+        int64_t b = q.rp[v];
+        r.p = q.col + b;
+        r.n = q.rp[v + 1] - b;
+    }
+    return r;
+}
+
+struct WarpState {
+    int32_t emb[GZ_MAX_K];     // bound vertices e_0..e_{k-1}
+    int64_t itp[GZ_MAX_K];     // index of e_t within loop t's candidate list
+    int64_t blen[GZ_MAXBUF];   // current length of each scratch buffer
+};
+
+// Executes one compiled set operation (see GzOp).
+__device__ void exec_op(const KQ& q, const GzOp& op, WarpState& ws, int32_t* scratch, int lane,
+                        unsigned long long& acc, int* status) {
+    const bool bounded = op.bound_pos >= 0;
+    const int32_t beta = bounded ? ws.emb[op.bound_pos] : INT_MAX;
+    const int32_t* L;
+    int64_t nL;
+    if (op.left_buf >= 0) {
+        L = scratch + q.buf_off[op.left_buf];
+        nL = ws.blen[op.left_buf];
+        if (op.left_iter) nL = ws.itp[op.level];
+        else if (bounded) nL = warp_lower_bound_rw(L, nL, beta, lane);
+    } else {
+        ListRef r = adj_list(q, ws.emb[op.left_pos], op.left_dag);
+        L = r.p;
+        nL = r.n;
+        if (op.left_iter) nL = ws.itp[op.level];
+        else if (bounded && op.left_dag != 2) nL = warp_lower_bound(L, nL, beta, lane);
+    }
+    ListRef R[GZ_MAXRIGHT];
+    const int nr = op.nright;
+    for (int r = 0; r < nr; ++r) R[r] = adj_list(q, ws.emb[op.right_pos[r]], op.right_dag[r]);
+
+    const bool count_only = op.dst < 0;
+    int32_t* out = count_only ? nullptr : scratch + q.buf_off[op.dst];
+    const int64_t cap = count_only ? 0 : q.buf_cap[op.dst];
+    int64_t w = 0;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (int64_t base = 0; base < nL; base += 32) {
+        int64_t idx = base + lane;
+        bool keep = idx < nL;
+        int32_t x = keep ? L[idx] : 0;
+        for (int r = 0; r < nr && keep; ++r) {
+            bool f = contains(R[r].p, (int)R[r].n, x);
+            keep = f != (op.right_sub[r] != 0);
+        }
+        if (count_only) {
+            if (keep && op.excl_mask) {
+                for (int j = 0; j < GZ_MAX_K; ++j)
+                    if ((op.excl_mask >> j & 1) && ws.emb[j] == x) keep = false;
+            }
+            acc += keep ? 1ull : 0ull;
+        } else {
+            unsigned m = __ballot_sync(kFull, keep);
+            int64_t pos = w + __popc(m & lt_mask);
+            if (keep) {
+                if (pos < cap) out[pos] = x;
+                else atomicExch(status, 1);
+            }
+            w += __popc(m);
+        }
+    }
+    if (!count_only) {
+        ws.blen[op.dst] = w < cap ? w : cap;
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ void run_level(const KQ& q, int t, WarpState& ws, int32_t* scratch,
+                                          int lane, unsigned long long& acc, int* status) {
+    const GzProg& P = q.prog;
+    for (int i = P.level_begin[t]; i < P.level_end[t]; ++i) exec_op(q, P.ops[i], ws, scratch, lane, acc, status);
+}
+
+// Candidate list of loop d (2 <= d <= k-2) once e_{d-1} is bound.
+__device__ __forceinline__ ListRef cand_list(const KQ& q, int d, const WarpState& ws,
+                                             int32_t* scratch, int lane) {
+    const GzProg& P = q.prog;
+    ListRef r;
+    if (P.cand_buf[d] >= 0) {
+        r.p = scratch + q.buf_off[P.cand_buf[d]];
+        r.n = ws.blen[P.cand_buf[d]];
+    } else {
+        r = adj_list(q, ws.emb[P.cand_pos[d]], P.cand_dag[d]);
+        if (P.cand_bound[d] >= 0 && P.cand_dag[d] != 2)
+            r.n = warp_lower_bound(r.p, r.n, ws.emb[P.cand_bound[d]], lane);
+    }
+    return r;
+}
+
+__device__ void process_unit(const KQ& q, int64_t unit, WarpState& ws, int32_t* scratch, int lane,
+                             unsigned long long& acc, int* status) {
+    const GzProg& P = q.prog;
+    const int k = P.k;
+    const int32_t e0 = q.usrc[unit];
+    const int32_t e1 = q.ucol[unit];
+    ws.emb[0] = e0;
+    ws.emb[1] = e1;
+    ws.itp[1] = unit - q.urp[e0];
+    if (k == 2) {
+        if (lane == 0) acc += 1;
+        return;
+    }
+    run_level(q, 1, ws, scratch, lane, acc, status);
+    if (k == 3) return;
+    // explicit DFS over loops 2..k-2
+    const int32_t* cp[GZ_MAX_K];
+    int64_t cn[GZ_MAX_K], it[GZ_MAX_K];
+    int d = 2;
+    {
+        ListRef r = cand_list(q, 2, ws, scratch, lane);
+        cp[2] = r.p; cn[2] = r.n; it[2] = 0;
+    }
+    while (d >= 2) {
+        if (it[d] >= cn[d]) { --d; continue; }
+        const int64_t pos = it[d]++;
+        const int32_t c = cp[d][pos];
+        bool skip = false;
+        const uint8_t ex = P.cand_excl[d];
+        if (ex)
+            for (int j = 0; j < d; ++j)
+                if ((ex >> j & 1) && ws.emb[j] == c) skip = true;
+        if (skip) continue;
+        ws.emb[d] = c;
+        ws.itp[d] = pos;
+        run_level(q, d, ws, scratch, lane, acc, status);
+        if (d < k - 2) {
+            ++d;
+            ListRef r = cand_list(q, d, ws, scratch, lane);
+            cp[d] = r.p; cn[d] = r.n; it[d] = 0;
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    return v;
+}
+
+// Persistent enumeration kernel over a batch of queries (nq >= 1).
+__global__ void __launch_bounds__(512) k_enumerate(const KQ* __restrict__ qs, int nq,
+                                                   int64_t total_units, int chunk,
+                                                   unsigned long long* __restrict__ work,
+                                                   unsigned long long* __restrict__ counts,
+                                                   int* __restrict__ status,
+                                                   int32_t* __restrict__ scratch,
+                                                   int64_t words_per_warp) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int32_t* my = scratch + gwarp * words_per_warp;
+    WarpState ws;
+    unsigned long long acc = 0;
+    int cur = -1;
+    for (;;) {
+        unsigned long long start = 0;
+        if (lane == 0) start = atomicAdd(work, (unsigned long long)chunk);
+        start = __shfl_sync(kFull, start, 0);
+        if ((int64_t)start >= total_units) break;
+        int64_t end = (int64_t)start + chunk;
+        if (end > total_units) end = total_units;
+        for (int64_t u = (int64_t)start; u < end; ++u) {
+            if (cur < 0 || u < qs[cur].unit_begin || u >= qs[cur].unit_begin + qs[cur].unit_count) {
+                if (cur >= 0) {
+                    unsigned long long s = warp_sum(acc);
+                    if (lane == 0 && s) atomicAdd(&counts[cur], s);
+                    acc = 0;
+                }
+                int lo = 0, hi = nq - 1;  // last query with unit_begin <= u
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (qs[mid].unit_begin <= u) lo = mid; else hi = mid - 1;
+                }
+                cur = lo;
+            }
+            const KQ& q = qs[cur];
+            process_unit(q, q.unit_lo + (u - q.unit_begin), ws, my, lane, acc, status);
+        }
+    }
+    if (cur >= 0) {
+        unsigned long long s = warp_sum(acc);
+        if (lane == 0 && s) atomicAdd(&counts[cur], s);
+    }
+}
+
+}  // namespace
+
+uint64_t scratch_words_per_warp(const GzProg& p, const gz_graph& g, const GzView& v) {
+    uint64_t w = 0;
+    for (int b = 0; b < p.nbuf; ++b) {
+        uint64_t cap = (uint64_t)(p.buf_dag[b] ? v.max_out : g.max_deg);
+        w += (cap + 31) & ~31ull;
+    }
+    return w;
+}
+
+int resident_warps(const LaunchCfg& cfg) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate, cfg.block_warps * 32, 0);
+    if (per_sm < 1) per_sm = 1;
+    int blocks = cfg.blocks > 0 ? cfg.blocks : sms * per_sm;
+    return blocks * cfg.block_warps;
+}
+
+// Builds the per-query descriptors, then one persistent launch. d_counts[nq] must
+// be zeroed by the caller (on stream s); scratch must hold resident_warps(cfg) *
+// max words per warp int32 words.
+gz_status count_launch(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream_t s,
+                       unsigned long long* d_counts, void* scratch, uint64_t scratch_bytes,
+                       int* d_status) {
+    if (nq <= 0) return GZ_OK;
+    std::vector<KQ> h(nq);
+    int64_t total = 0;
+    uint64_t words = 0;
+    for (int i = 0; i < nq; ++i) {
+        const Query& Q = qs[i];
+        KQ& k = h[i];
+        memset(&k, 0, sizeof(KQ));
+        k.prog = *Q.prog;
+        const GzView& v = *Q.view;
+        k.rp = v.rp; k.col = v.col; k.drp = v.dag_rp; k.dcol = v.dag_col;
+        if (Q.prog->unit_dag) { k.usrc = v.dag_src; k.ucol = v.dag_col; k.urp = v.dag_rp; }
+        else { k.usrc = v.src; k.ucol = v.col; k.urp = v.rp; }
+        k.unit_lo = Q.unit_lo;
+        k.unit_count = Q.unit_hi - Q.unit_lo;
+        k.unit_begin = total;
+        total += k.unit_count;
+        uint64_t off = 0;
+        for (int b = 0; b < Q.prog->nbuf; ++b) {
+            uint64_t cap = (uint64_t)(Q.prog->buf_dag[b] ? v.max_out : Q.g->max_deg);
+            k.buf_off[b] = (int64_t)off;
+            k.buf_cap[b] = (int64_t)cap;
+            off += (cap + 31) & ~31ull;
+        }
+        if (off > words) words = off;
+    }
+    if (total == 0) return GZ_OK;
+    const int warps = resident_warps(cfg);
+    if ((uint64_t)warps * words * sizeof(int32_t) > scratch_bytes) {
+        set_error("count: scratch too small (%llu bytes needed)",
+                  (unsigned long long)((uint64_t)warps * words * 4));
+        return GZ_ENOMEM;
+    }
+    KQ* d = nullptr;
+    unsigned long long* work = nullptr;
+    cudaError_t e = cudaMallocAsync(&d, sizeof(KQ) * nq + 16, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync queries");
+    work = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(d) + sizeof(KQ) * nq);
+    e = cudaMemcpyAsync(d, h.data(), sizeof(KQ) * nq, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(work, 0, 16, s);
+    if (e == cudaSuccess) {
+        const int blocks = warps / cfg.block_warps;
+        k_enumerate<<<blocks, cfg.block_warps * 32, 0, s>>>(
+            d, nq, total, cfg.chunk > 0 ? cfg.chunk : 1, work, d_counts, d_status,
+            reinterpret_cast<int32_t*>(scratch), (int64_t)words);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(d, s);
+    if (e != cudaSuccess) return cuda_fail(e, "enumerate launch");
+    return GZ_OK;
+}
+
+}  // namespace gz

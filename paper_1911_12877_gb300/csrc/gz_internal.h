@@ -1,0 +1,119 @@
+// gz_internal.h - data structures shared by the host planner and the CUDA kernels
+// of libgz. Not part of the public C ABI (include/gz.h is).
+#pragma once
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+#include "../../include/gz.h"
+
+#define GZ_MAXOPS 40
+#define GZ_MAXBUF 24
+#define GZ_MAXRIGHT 7
+
+// One set operation of the compiled nested loops. It runs right after e_level is
+// bound. out = left[<b] filtered by each right list N(e_pos)[<b] (present for an
+// intersection, absent for a difference), b = e_bound_pos or +inf (Sec. 6: the
+// restriction's vertex id bounds the scan).
+struct GzOp {
+    int8_t level;      // t: executed once e_t is fixed
+    int8_t dst;        // scratch buffer written, or -1: count only (last loop)
+    int8_t left_buf;   // scratch buffer of the left operand, or -1: a view of N(e_left_pos)
+    int8_t left_pos;   // list owner when left_buf == -1
+    int8_t left_dag;   // left view lies inside the owner's out-list (bound <= owner)
+    int8_t left_iter;  // left[<b] is exactly the first i_t entries of level t's candidates
+    int8_t nright;
+    int8_t bound_pos;  // -1 = unbounded
+    int8_t right_pos[GZ_MAXRIGHT];
+    int8_t right_sub[GZ_MAXRIGHT];  // 0 = intersect, 1 = subtract
+    int8_t right_dag[GZ_MAXRIGHT];  // 1 = bounded part lies in the out-list; 2 = whole out-list
+    uint8_t excl_mask;              // count ops: positions whose vertex is not counted
+};
+
+// Device-side program: the schedule compiled into per-loop operation lists.
+struct GzProg {
+    int32_t k;
+    int32_t nops;
+    int32_t nbuf;
+    int32_t unit_dag;                 // level-1 candidates are out-lists (bp[1] == 0)
+    GzOp ops[GZ_MAXOPS];
+    int8_t level_begin[GZ_MAX_K];     // ops[level_begin[t] .. level_end[t]) run at loop t
+    int8_t level_end[GZ_MAX_K];
+    // candidates of loop d (2 <= d <= k-2); loop 1 candidates come from the work unit
+    int8_t cand_buf[GZ_MAX_K];        // buffer, or -1: view of N(e_cand_pos)[<e_cand_bound]
+    int8_t cand_pos[GZ_MAX_K];
+    int8_t cand_bound[GZ_MAX_K];
+    int8_t cand_dag[GZ_MAX_K];
+    uint8_t cand_excl[GZ_MAX_K];      // positions whose vertex is skipped
+    int8_t buf_dag[GZ_MAXBUF];        // 1: contents bounded by the max out-degree
+};
+
+// Host-side plan (opaque gz_plan).
+struct gz_plan {
+    int k;
+    uint8_t adj[GZ_MAX_K * GZ_MAX_K];  // pattern, labels
+    int32_t order[GZ_MAX_K];           // schedule (labels)
+    int32_t bp[GZ_MAX_K];              // bound parent per schedule position, -1 none
+    uint64_t aut_size;
+    double est_cost;
+    GzProg prog;
+};
+
+// CSR view on the device.
+struct GzCsr {
+    const int64_t* rp;   // [n+1]
+    const int32_t* col;  // [nnz]
+};
+
+// Device graph (opaque gz_graph).
+struct GzView {
+    // one id space: the original ids, or the degree-reindexed ones
+    int64_t* rp = nullptr;       // full CSR
+    int32_t* col = nullptr;
+    int64_t* dag_rp = nullptr;   // out-lists: N(v) intersect [0, v)
+    int32_t* dag_col = nullptr;
+    int32_t* dag_src = nullptr;  // source vertex of each out-list entry
+    int32_t* src = nullptr;      // source vertex of each full-CSR entry (built on demand)
+    int64_t dag_nnz = 0;
+    int64_t max_out = 0;
+    bool owned_csr = true;
+    bool has_dag = false;
+};
+
+struct gz_graph {
+    int64_t n = 0, nnz = 0, max_deg = 0;
+    int device = 0;
+    GzView orig;
+    GzView ori;            // oriented view (after gz_orient)
+    int32_t* new_id = nullptr;  // old -> new id
+    bool oriented = false;
+};
+
+namespace gz {
+
+void set_error(const char* fmt, ...);
+gz_status cuda_fail(cudaError_t e, const char* what);
+
+// graph side (gz_graph.cu)
+gz_status build_dag(gz_graph* g, GzView* v, cudaStream_t s);
+gz_status build_src(gz_graph* g, GzView* v, cudaStream_t s);
+gz_status orient(gz_graph* g, cudaStream_t s);
+
+// counting side (gz_count.cu)
+struct Query {
+    const GzProg* prog;   // host pointer to the program
+    const gz_graph* g;
+    const GzView* view;
+    int64_t unit_lo, unit_hi;  // work units (edges of the unit CSR) in this launch
+};
+struct LaunchCfg {
+    int block_warps = 8;  // warps per CTA
+    int chunk = 4;        // work units per queue pop
+    int blocks = 0;       // 0 = auto (resident CTAs on every SM)
+};
+uint64_t scratch_words_per_warp(const GzProg& p, const gz_graph& g, const GzView& v);
+gz_status count_launch(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream_t s,
+                       unsigned long long* d_counts, void* scratch, uint64_t scratch_bytes,
+                       int* d_status);
+int resident_warps(const LaunchCfg& cfg);
+
+}  // namespace gz

@@ -1,0 +1,276 @@
+"""GPU parity: libgz's CUDA path against the CPU oracle, bit-exact (counts are
+integers, so the tolerance is zero).
+
+Inputs are the seeded synthetic graphs of ``synthetic``; expected values come
+from ``oracle`` only (computed here, or stored by tests/golden/make_golden.py).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic as S
+from synthetic.patterns import BATCH_PATTERNS, EDGES, PATTERN_SET, adjacency
+
+gz = pytest.importorskip("paper_1911_12877_gb300")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+SMALL_NAMES = ["edge", "wedge", "triangle", "path4", "star3", "c4", "paw", "diamond", "k4", "c5",
+               "house", "hourglass", "chordal5", "k5", "k6", "chordal6", "asym6"]
+
+
+_ORACLE_CACHE = {}
+
+
+def oracle_count(name_or_adj, g, oriented=True, lo=0, hi=None):
+    """Oracle B count. The count does not depend on the labelling (pinned in
+    test_oracle), and on the degree-reindexed graph the oracle's bounded scans
+    are far shorter, so it runs there by default."""
+    a = adjacency(name_or_adj) if isinstance(name_or_adj, str) else name_or_adj
+    key = (a.tobytes(), g.name, g.n, g.nnz, oriented, lo, hi)
+    if g.name and key in _ORACLE_CACHE:
+        return _ORACLE_CACHE[key]
+    order, _ = O.choose_schedule(a)
+    if oriented:
+        g, _ = O.reindex(g)
+    r = O.count_nested(a, order, g, lo, hi)[0]
+    _ORACLE_CACHE[key] = r
+    return r
+
+
+@pytest.fixture(scope="module")
+def tiny_graphs():
+    return [S.random_small(12, 0.45, 21), S.random_small(30, 0.2, 22), S.random_small(40, 0.12, 23)]
+
+
+@pytest.mark.parametrize("name", SMALL_NAMES)
+def test_tiny_graphs_every_schedule(name, tiny_graphs):
+    a = adjacency(name)
+    for g in tiny_graphs:
+        G = gz.Graph.from_csr(g, validate=gz.GZ_VALIDATE_SYMMETRIC).orient()
+        want = oracle_count(a, g)
+        for s in O.distinct_schedules(a)[:6]:
+            p = gz.Plan(a, order=s)
+            assert gz.count(p, G, orientation=False) == want, (name, s)
+            assert gz.count(p, G, orientation=True) == want, (name, s, "oriented")
+
+
+@pytest.mark.parametrize("graph", ["empty0", "empty7", "star", "K8", "K34", "petersen", "C6",
+                                   "hub_last", "two_comp"])
+def test_structured_edge_cases(graph):
+    g = {
+        "empty0": lambda: S.empty(0), "empty7": lambda: S.empty(7), "star": lambda: S.star(40),
+        "K8": lambda: S.complete(8), "K34": lambda: S.complete_bipartite(3, 4),
+        "petersen": S.petersen, "C6": lambda: S.cycle(6),
+        "hub_last": lambda: S.from_edges(50, [(49, i) for i in range(49)] + [(0, 1), (2, 3)]),
+        "two_comp": lambda: S.from_edges(12, [(i, j) for i in range(5) for j in range(i + 1, 5)]
+                                         + [(6, 7), (7, 8), (8, 9), (9, 6)]),
+    }[graph]()
+    G = gz.Graph.from_csr(g, validate=gz.GZ_VALIDATE_SYMMETRIC).orient()
+    for name in ["edge", "wedge", "triangle", "c4", "star3", "diamond", "k4", "c5", "k5"]:
+        want = O.count_brute_induced(adjacency(name), g) if g.n <= 50 and len(adjacency(name)) <= 4 \
+            else oracle_count(name, g)
+        p = gz.Plan(name)
+        assert gz.count(p, G, False) == want, (graph, name)
+        assert gz.count(p, G, True) == want, (graph, name, "oriented")
+
+
+@pytest.mark.parametrize("which", ["er", "rmat12", "rmat16"])
+def test_orientation_matches_oracle_relabel(which):
+    g = {"er": S.er_triangle, "rmat12": lambda: S.rmat(12, 16, 5),
+         "rmat16": lambda: S.rmat(16, 8, 6)}[which]()
+    G = gz.Graph.from_csr(g).orient()
+    rp, col, nid = G.export(oriented=True)
+    orp, ocol = O.reindex(g)[0].row_ptr, O.reindex(g)[0].col
+    onid = O.reindex(g)[1]
+    assert (nid == onid).all()
+    assert (rp == orp).all()
+    assert (col == ocol).all()
+    info = G.info()
+    split = [int(np.searchsorted(ocol[orp[v]:orp[v + 1]], v)) for v in range(g.n)]
+    assert info["max_out_degree_oriented"] == max(split)
+    assert info["max_degree"] == int(np.diff(g.row_ptr).max())
+
+
+def test_reorient_is_repeatable():
+    g = S.rmat(13, 16, 7)
+    G = gz.Graph.from_csr(g).orient()
+    a = G.export(oriented=True)
+    G.orient()
+    b = G.export(oriented=True)
+    for x, y in zip(a, b):
+        assert (x == y).all()
+
+
+def test_er_triangle_workload():
+    # Triangle counting, plain method on the original ids: G(4096, 16/4095), seed 1.
+    g = S.er_triangle()
+    G = gz.Graph.from_csr(g, validate=gz.GZ_VALIDATE_SYMMETRIC)
+    want = oracle_count("triangle", g)
+    assert gz.count(gz.Plan("triangle"), G, orientation=False) == want
+    G.orient()
+    assert gz.count(gz.Plan("triangle"), G, orientation=True) == want
+
+
+@pytest.mark.parametrize("name", ["wedge", "triangle", "path4", "star3", "c4", "paw", "diamond",
+                                  "k4", "house", "chordal5", "k5", "chordal6", "hourglass", "c5"])
+def test_rmat_medium_all_patterns(name):
+    g = S.rmat(11, 8, 31)  # 2048 vertices, ragged hub lists
+    G = gz.Graph.from_csr(g).orient()
+    want = oracle_count(name, g)
+    p = gz.Plan(name)
+    assert gz.count(p, G, True) == want
+    assert gz.count(p, G, False) == want
+
+
+def test_root_ranges_partition_count():
+    g = S.rmat(14, 16, 9)
+    G = gz.Graph.from_csr(g).orient()
+    p = gz.Plan("diamond")
+    total = gz.count(p, G, True)
+    cuts = [0, 1, 7, 100, 1000, 5000, g.n]
+    parts = [gz.count(p, G, True, lo, hi) for lo, hi in zip(cuts[:-1], cuts[1:])]
+    assert sum(parts) == total
+    go, _ = O.reindex(g)
+    order, _ = O.choose_schedule(adjacency("diamond"))
+    for (lo, hi), c in zip(zip(cuts[:-1], cuts[1:]), parts):
+        if hi - lo <= 1000:
+            assert c == O.count_nested(adjacency("diamond"), order, go, lo, hi)[0]
+
+
+@pytest.mark.parametrize("bw,chunk", [(4, 1), (8, 4), (16, 16), (8, 64)])
+def test_launch_shapes_do_not_change_counts(bw, chunk):
+    g = S.rmat(13, 16, 10)
+    G = gz.Graph.from_csr(g).orient()
+    for name in ["k4", "c4", "diamond"]:
+        p = gz.Plan(name)
+        assert gz.count(p, G, True, block_warps=bw, chunk=chunk) == oracle_count(name, g)
+
+
+def test_autotune_keeps_count():
+    g = S.rmat(13, 16, 11)
+    G = gz.Graph.from_csr(g).orient()
+    p = gz.Plan("k4")
+    want = gz.count(p, G, True)
+    bw, ch = gz.autotune(p, G, True)
+    assert bw in (4, 8, 16) and ch in (1, 4, 16)
+    assert gz.count(p, G, True) == want == oracle_count("k4", g)
+
+
+def test_batch_equals_alone():
+    graphs = [S.rmat(10, 8, 100), S.rmat(12, 16, 101), S.er_triangle(), S.rmat(11, 32, 102)]
+    Gs = [gz.Graph.from_csr(g).orient() for g in graphs]
+    plans = {n: gz.Plan(n) for n in BATCH_PATTERNS}
+    qp, qg, qo = [], [], []
+    for i, n in enumerate(BATCH_PATTERNS):
+        for j in range(len(Gs)):
+            if (i + j) % 2 == 0:
+                qp.append(plans[n]); qg.append(Gs[j]); qo.append((i + j) % 4 == 0)
+    got = gz.count_batch(qp, qg, qo)
+    alone = [gz.count(p, G, o) for p, G, o in zip(qp, qg, qo)]
+    assert got == alone
+    idx = {id(G): graphs[j] for j, G in enumerate(Gs)}
+    for p, G, c in zip(qp, qg, got):
+        name = [n for n, pp in plans.items() if pp is p][0]
+        if name in ("triangle", "k4", "diamond", "c4", "k5"):
+            assert c == oracle_count(name, idx[id(G)])
+
+
+def test_server_equals_alone():
+    g = S.rmat(12, 16, 50)
+    G = gz.Graph.from_csr(g).orient()
+    names = ["triangle", "c4", "diamond", "k4", "k5", "chordal5"]
+    plans = [gz.Plan(n) for n in names]
+    alone = [gz.count(p, G, True) for p in plans]
+    srv = gz.Server(max_inflight=3, max_batch=8)
+    rng = np.random.default_rng(5)
+    pidx = rng.integers(0, len(names), 60).astype(np.int32)
+    arr = np.cumsum(rng.exponential(2e5, 60)).astype(np.int64)  # ~5000 req/s
+    counts, lat, stats = srv.replay(plans, [G], [1] * 60, arr, pidx, np.zeros(60, np.int32))
+    assert [int(c) for c in counts] == [alone[i] for i in pidx]
+    assert (lat > 0).all()
+    counts_f, lat_f, stats_f = srv.replay(plans, [G], [1] * 60, arr, pidx, np.zeros(60, np.int32),
+                                          fifo=True)
+    assert [int(c) for c in counts_f] == [alone[i] for i in pidx]
+    assert stats_f["launches"] == 60
+    t = [srv.submit(plans[i], G, True) for i in range(len(plans))]
+    assert [srv.wait(x)[0] for x in t] == alone
+    srv.close()
+
+
+def test_device_pointer_graph():
+    import torch
+    g = S.rmat(12, 16, 60)
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    col = torch.from_numpy(g.col).cuda()
+    G = gz.Graph(rp, col, validate=gz.GZ_VALIDATE_SYMMETRIC).orient()
+    assert gz.count(gz.Plan("k4"), G, True) == oracle_count("k4", g)
+
+
+@pytest.mark.parametrize("bad", ["unsorted", "selfloop", "range", "dup", "asym", "rowptr"])
+def test_invalid_csr_rejected(bad):
+    g = S.complete(5)
+    rp, col = g.row_ptr.copy(), g.col.copy()
+    if bad == "unsorted":
+        col[0], col[1] = col[1], col[0]
+    elif bad == "selfloop":
+        col[0] = 0
+    elif bad == "range":
+        col[0] = 99
+    elif bad == "dup":
+        col[1] = col[0]
+    elif bad == "asym":  # 0 -> 1 without 1 -> 0
+        rp = np.array([0, 1, 1], dtype=np.int64)
+        col = np.array([1], dtype=np.int32)
+    elif bad == "rowptr":
+        rp[2] = rp[1] - 1
+    with pytest.raises(gz.GzError) as e:
+        gz.Graph(rp, col, validate=gz.GZ_VALIDATE_SYMMETRIC)
+    assert e.value.status == gz.GZ_EINVAL
+
+
+def test_orientation_needed_for_oriented_count():
+    G = gz.Graph.from_csr(S.complete(6))
+    with pytest.raises(gz.GzError):
+        gz.count(gz.Plan("triangle"), G, orientation=True)
+
+
+# ------------------------------------------------------------ full-size workloads
+
+def _golden(name):
+    path = os.path.join(GOLDEN, name)
+    if not os.path.exists(path):
+        pytest.skip(f"golden file {name} missing")
+    return json.load(open(path))
+
+
+def test_clique_rmat20_full_and_sampled():
+    """k-clique workload (R-MAT scale 20, ef 16, seed 20, oriented), in the launch
+    configuration the bench times: K4 in full against the stored oracle count, K5 on
+    sampled root ranges against the oracle computed here."""
+    gold = _golden("clique_rmat20.json")
+    g = S.rmat_clique()
+    assert g.nnz == gold["nnz"]
+    G = gz.Graph.from_csr(g).orient()
+    k4, k5 = gz.Plan("k4"), gz.Plan("k5")
+    assert gz.count(k4, G, True) == gold["k4"]["count"]
+    for (lo, hi, c) in gold["k5"]["samples"]:
+        assert gz.count(k5, G, True, lo, hi) == c, (lo, hi)
+    if "count" in gold["k5"]:
+        assert gz.count(k5, G, True) == gold["k5"]["count"]
+
+
+def test_patterns_rmat22_sampled():
+    """Arbitrary-pattern workload (R-MAT scale 22, ef 16, seed 22, oriented):
+    sampled root ranges against stored oracle counts."""
+    gold = _golden("patterns_rmat22.json")
+    g = S.rmat_patterns()
+    assert g.nnz == gold["nnz"]
+    G = gz.Graph.from_csr(g).orient()
+    for name, rec in gold["patterns"].items():
+        p = gz.Plan(name)
+        for (lo, hi, c) in rec["samples"]:
+            assert gz.count(p, G, True, lo, hi) == c, (name, lo, hi)
