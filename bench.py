@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Benchmark of the GraphZero counting hot path on GB300 (one JSON line on rank 0).
+
+Default workload (k-clique counting with degree orientation): R-MAT scale 20,
+edge factor 16, (a, b, c, d) = (0.57, 0.19, 0.19, 0.05), seed 20; one step =
+plan K4 and K5 (host planner), orient the device-resident graph (GPU reindex +
+out-list build), count K4 and K5 (GPU enumeration, exact uint64), counts back
+to the host. Metric: intersected elements per second, E / step time, where E is
+the number of list elements the bounded linear scans of the paper's nested
+loops consume (computed by the CPU oracle and stored in tests/golden).
+
+Other workloads (--config): triangle (ER 4096, plain method), patterns (R-MAT
+22, five patterns), batched (64 queries over 16 graphs, one launch vs one per
+launch), served (Poisson request stream on R-MAT 24 vs FIFO one-per-launch).
+
+--impl reference times the CPU oracle on a bounded sample of the same workload.
+Under torchrun each rank runs a replica of the workload on its own GPU (weak
+scaling, no collective on the data path); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "intersected elements/s (count time; E/t as % of HBM peak)"
+UNIT = "elem/s"
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+PROFILES = os.path.join(ROOT, "profiles")
+
+
+# ------------------------------------------------------------------ distributed helpers
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def init_dist(world, backend):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def aggregate(dist, elapsed_s: float, units: float):
+    """Max of elapsed over ranks and sum of units over ranks (whole-job totals)."""
+    if dist is None:
+        return elapsed_s, units
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([elapsed_s], dtype=torch.float64, device=dev)
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+# ------------------------------------------------------------------ measurement helpers
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("gz_count.cu", "gz_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1911_12877_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(name: str):
+    """Per-launch DRAM bytes from a committed ncu summary, if taken on this kernel source."""
+    path = os.path.join(PROFILES, name)
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    if d.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def flush_l2(buf):
+    buf.add_(1)  # writes a buffer larger than L2 (129 MB)
+
+
+# ------------------------------------------------------------------ workloads
+
+def load_golden(name):
+    path = os.path.join(GOLDEN, name)
+    if not os.path.exists(path):
+        raise SystemExit(f"missing {path}: run tests/golden/make_golden.py")
+    return json.load(open(path))
+
+
+def clique_workload():
+    import synthetic as S
+    g = S.rmat_clique()
+    gold = load_golden("clique_rmat20.json")
+    if gold["nnz"] != g.nnz:
+        raise SystemExit("golden clique_rmat20.json does not match the generated graph")
+    return g, gold
+
+
+def cpu_baseline_clique(g, gold, target_s: float = 12.0, max_s: float = 40.0):
+    """The oracle as it stands on a bounded sample: roots in 16 evenly spaced
+    ranges of width w of the reindexed graph, K4 and K5, all host threads."""
+    import oracle as O
+    from synthetic.patterns import adjacency
+    go, _ = O.reindex(g)
+    pats = [(adjacency("k4"), gold["k4"]["order"]), (adjacency("k5"), gold["k5"]["order"])]
+    starts = [i * (g.n // 16) + 4096 for i in range(16)]  # skip the very top hubs
+    w, t, e = 1, 0.0, 0
+    while True:
+        t0 = time.perf_counter()
+        e = 0
+        for a, order in pats:
+            for s in starts:
+                e += O.count_nested(a, order, go, s, min(g.n, s + w))[1]
+        t = time.perf_counter() - t0
+        if t >= target_s or t * 2 > max_s or w >= g.n // 16:
+            break
+        w = max(w * 2, int(w * target_s / max(t, 1e-3) * 0.9))
+    return {"value": e / t, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+            "sample": f"K4+K5 on R-MAT 20 (reindexed), roots in 16 ranges of {w} ids "
+                      f"starting at i*n/16+4096; E={e} in {t:.2f} s"}, w, starts
+
+
+def run_clique(args, dist, world, rank, local):
+    import torch
+    import paper_1911_12877_gb300 as gz
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    g, gold = clique_workload()
+    e_k4, e_k5 = gold["k4"]["elems"], gold["k5"]["elems"]
+    e_total = e_k4 + e_k5
+    G = gz.Graph.from_csr(g)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    k5_ev = []
+
+    def step(record=False):
+        p4, p5 = gz.Plan("k4"), gz.Plan("k5")  # planner (host)
+        G.orient()
+        c4 = gz.count(p4, G, orientation=True)
+        if record:
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        c5 = gz.count(p5, G, orientation=True)
+        if record:
+            b.record(stream)
+            k5_ev.append((a, b))
+        return c4, c5
+
+    for _ in range(args.warmup):
+        counts = step()
+    if counts[0] != gold["k4"]["count"]:
+        raise SystemExit(f"K4 count {counts[0]} != oracle {gold['k4']['count']}")
+    barrier(dist)
+    torch.cuda.synchronize()
+    launches0 = gz.kernel_launches()
+    evs = []
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            counts = step(record=True)
+            b.record(stream)
+            evs.append((a, b))
+            if i + 1 < args.steps:
+                flush_l2(flush)
+        torch.cuda.synchronize()
+    launches = gz.kernel_launches() - launches0
+    barrier(dist)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    k5_ms = [a.elapsed_time(b) for a, b in k5_ev]
+    elapsed = sum(step_ms) / 1e3
+    elapsed_max, units = aggregate(dist, elapsed, e_total * args.steps)
+    value = units / elapsed_max
+    peak, peak_kind = measured_peaks()
+    k5_s = statistics.mean(k5_ms) / 1e3
+    achieved = 4.0 * e_k5 / k5_s / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_enumerate (K5)", "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": profiled_traffic("k_enumerate_k5_rmat20.json"),
+                "peak_kind": peak_kind, "kernel_ms": round(k5_s * 1e3, 3),
+                "algorithmic_bytes": 4 * e_k5}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timing
+    e2e = None
+    if not args.no_e2e:
+        rp_h = torch.from_numpy(g.row_ptr).pin_memory()
+        col_h = torch.from_numpy(g.col).pin_memory()
+        import ctypes
+        e2e_t = []
+        for i in range(max(1, args.steps)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = ctypes.c_void_p()
+            gz._check(gz.lib().gz_load_csr(rp_h.data_ptr(), col_h.data_ptr(), g.n, g.nnz, 0, 0,
+                                           stream.cuda_stream, ctypes.byref(h)), "gz_load_csr")
+            Gh = gz.Graph.__new__(gz.Graph)
+            Gh.handle, Gh.n, Gh.nnz, Gh._keep = h, g.n, g.nnz, None
+            Gh.orient()
+            p4, p5 = gz.Plan("k4"), gz.Plan("k5")
+            c = (gz.count(p4, Gh, True), gz.count(p5, Gh, True))
+            Gh.close()
+            torch.cuda.synchronize()
+            e2e_t.append(time.perf_counter() - t0)
+            if c != counts:
+                raise SystemExit("end-to-end counts differ from the device-resident run")
+        t_e2e, u_e2e = aggregate(dist, sum(e2e_t), e_total * len(e2e_t))
+        e2e = {"value": u_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * (g.n + 1) + 4 * g.nnz,
+               "d2h_bytes_per_step": 16, "ms_per_step": round(1e3 * t_e2e / len(e2e_t), 3)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_clique(g, gold)[0]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 * elapsed_max / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": "k-clique K4+K5 with degree orientation, R-MAT scale 20 ef 16 "
+                               "seed 20 (a,b,c,d)=(.57,.19,.19,.05)", "n": g.n, "nnz": g.nnz,
+                   "parallelism": f"replicas{world}", "l2": "flushed between timed steps",
+                   "step": "plan K4,K5 + GPU orient + count K4 + count K5"},
+        "counts": {"k4": counts[0], "k5": counts[1]},
+        "elems_per_step": e_total,
+        "step_ms": [round(x, 3) for x in step_ms],
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    return line
+
+
+def run_reference(args, world, rank):
+    """The reference arm: the CPU oracle, as it stands, on a bounded sample per step."""
+    if rank != 0:
+        return None
+    import oracle as O
+    from synthetic.patterns import adjacency
+    g, gold = clique_workload()
+    base, w, starts = cpu_baseline_clique(g, gold, target_s=6.0, max_s=20.0)
+    go, _ = O.reindex(g)
+    pats = [(adjacency("k4"), gold["k4"]["order"]), (adjacency("k5"), gold["k5"]["order"])]
+
+    def step():
+        e = 0
+        for a, order in pats:
+            for s in starts:
+                e += O.count_nested(a, order, go, s, min(g.n, s + w))[1]
+        return e
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    e = 0
+    for _ in range(args.steps):
+        e += step()
+    t = time.perf_counter() - t0
+    v = e / t
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": "k-clique K4+K5 with degree orientation, R-MAT scale 20 ef 16 "
+                                   "seed 20 (bounded root sample per step)", "n": g.n, "nnz": g.nnz},
+            "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle", "cores": O.threads(),
+                             "sample": base["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+EXTRA = {}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gz", choices=["gz", "reference"])
+    ap.add_argument("--config", default="clique",
+                    choices=["clique", "triangle", "patterns", "batched", "served"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "gz":
+        args.warmup = 3
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        line = run_reference(args, world, rank)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return 0
+    import torch
+    dist = init_dist(world, "nccl" if torch.cuda.is_available() else "gloo")
+    if args.config == "clique":
+        line = run_clique(args, dist, world, rank, local)
+    else:
+        line = EXTRA[args.config](args, dist, world, rank, local)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

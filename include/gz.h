@@ -145,7 +145,8 @@ gz_status gz_plan_schedules(int k, const uint8_t* adj, int32_t* orders, int cap,
 
 /*
  * Text listing of the compiled nested-loop program (one line per item, NUL
- * terminated, truncated to cap bytes): "unit dag=D", then per loop t its set
+ * terminated, truncated to cap bytes): "unit dag=D flat=F" (F: how the last loop is
+ * flattened across the candidates of loop k-2; 0 = not), then per loop t its set
  * operations "op level=t dst=B left_buf=B left_pos=P left_dag=D left_iter=I
  * bound=P excl=M rights=pos:sub:dag,..." and per loop d >= 2 its candidates
  * "cand d=.. buf=.. pos=.. bound=.. dag=.. excl=..", and "buf b dag=D" per
@@ -258,6 +259,9 @@ const char* gz_last_error(void);
 
 /* Library version string. */
 const char* gz_version(void);
+
+/* Number of CUDA kernels libgz has launched in this process (all streams). */
+uint64_t gz_kernel_launches(void);
 
 #ifdef __cplusplus
 }

@@ -63,6 +63,7 @@ def _lib():
     lib.orc_count_brute_induced.argtypes = [I, _u8p, L, _i64p, _i32p, _u64p]
     lib.orc_count_brute_injective.argtypes = [I, _u8p, L, _i64p, _i32p, _u64p]
     lib.orc_count_nested.argtypes = [I, _u8p, _i32p, L, _i64p, _i32p, L, L, I, _u64p, _u64p]
+    lib.orc_elems_nested.argtypes = [I, _u8p, _i32p, L, _i64p, _i32p, L, L, I, _u64p]
     lib.orc_elems_brute.argtypes = [I, _u8p, _i32p, L, _i64p, _i32p, _u64p]
     lib.orc_reindex.argtypes = [L, _i64p, _i32p, _i64p, _i32p, _i32p]
     return lib
@@ -181,6 +182,19 @@ def count_nested(adj, order, g, root_lo: int = 0, root_hi: int | None = None,
     _check(_lib().orc_count_nested(k, ap, op, g.n, rpp, colp, root_lo, hi, nthreads,
                                    ctypes.byref(cnt), ctypes.byref(el)), "nested")
     return cnt.value, el.value
+
+
+def elems_nested(adj, order, g, root_lo: int = 0, root_hi: int | None = None,
+                 nthreads: int = 0) -> int:
+    """E of Oracle B for roots in [root_lo, root_hi), without building the last loop's sets."""
+    a, k, ap = _adj(adj)
+    o, op = _order(order)
+    rp, col, rpp, colp = _csr(g)
+    el = ctypes.c_uint64()
+    hi = g.n if root_hi is None else root_hi
+    _check(_lib().orc_elems_nested(k, ap, op, g.n, rpp, colp, root_lo, hi, nthreads,
+                                   ctypes.byref(el)), "elems_nested")
+    return el.value
 
 
 def elems_brute(adj, order, g) -> int:

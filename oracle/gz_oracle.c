@@ -444,9 +444,41 @@ static inline int below(int32_t u, int32_t bound, int bounded) {
     return u < bound;
 }
 
-/* One level of the nested loops: build S_d from scratch, then recurse or count. */
+/* Number of elements of sorted L[0, len) below bound (all of them if unbounded). */
+static int64_t count_below(const int32_t* L, int64_t len, int32_t bound, int bounded) {
+    if (!bounded) return len;
+    int64_t lo = 0, hi = len;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (L[mid] < bound) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+/*
+ * E of the last loop without building its sets: every c in S_{k-2} (already
+ * built, matched vertices removed) is one partial embedding of the last loop,
+ * which adds sum_{j<k-1} |N(e_j) intersect [0, bound_{k-1})| with e_{k-2} = c.
+ */
+static void last_level_elems(const nplan* pl, int32_t* emb, const int32_t* S, int64_t n,
+                             uint64_t* el) {
+    const int k = pl->k, d = k - 1;
+    const int bounded = pl->bp[d] >= 0 && g_mut != MUT_NO_BOUND;
+    for (int64_t i = 0; i < n; ++i) {
+        emb[k - 2] = S[i];
+        int32_t bound = pl->bp[d] >= 0 ? emb[pl->bp[d]] : 0;
+        for (int j = 0; j < d; ++j) {
+            const int32_t* L = pl->col + pl->rp[emb[j]];
+            int64_t len = pl->rp[emb[j] + 1] - pl->rp[emb[j]];
+            *el += (uint64_t)count_below(L, len, bound, bounded);
+        }
+    }
+}
+
+/* One level of the nested loops: build S_d from scratch, then recurse or count.
+ * With elems_only set, the last loop only adds its E (no count is produced). */
 static void nested_level(const nplan* pl, int d, int32_t* emb, int32_t** buf, int32_t* tmp,
-                         uint64_t* cnt, uint64_t* el) {
+                         uint64_t* cnt, uint64_t* el, int elems_only) {
     const int k = pl->k;
     int bounded = pl->bp[d] >= 0 && g_mut != MUT_NO_BOUND;
     int32_t bound = pl->bp[d] >= 0 ? emb[pl->bp[d]] : 0;
@@ -493,9 +525,10 @@ static void nested_level(const nplan* pl, int d, int32_t* emb, int32_t** buf, in
         n = w;
     }
     if (d == k - 1) { *cnt += (uint64_t)n; return; }
+    if (elems_only && d == k - 2) { last_level_elems(pl, emb, S, n, el); return; }
     for (int64_t i = 0; i < n; ++i) {
         emb[d] = S[i];
-        nested_level(pl, d + 1, emb, buf, tmp, cnt, el);
+        nested_level(pl, d + 1, emb, buf, tmp, cnt, el, elems_only);
     }
 }
 
@@ -504,9 +537,32 @@ static void nested_level(const nplan* pl, int d, int32_t* emb, int32_t** buf, in
  * scheduled vertex lies in [root_lo, root_hi), and the element count E of
  * those roots. threads <= 0 uses the OpenMP default.
  */
+static int nested_run(int k, const uint8_t* adj, const int32_t* order, int64_t n,
+                      const int64_t* rp, const int32_t* col, int64_t root_lo, int64_t root_hi,
+                      int threads, uint64_t* count_out, uint64_t* elems_out, int elems_only);
+
 int orc_count_nested(int k, const uint8_t* adj, const int32_t* order, int64_t n,
                      const int64_t* rp, const int32_t* col, int64_t root_lo, int64_t root_hi,
                      int threads, uint64_t* count_out, uint64_t* elems_out) {
+    return nested_run(k, adj, order, n, rp, col, root_lo, root_hi, threads, count_out, elems_out, 0);
+}
+
+/*
+ * E only (the same value orc_count_nested reports), skipping the construction
+ * of the last loop's sets: their E needs only the bounded list lengths. For
+ * workloads whose last loop is too large for the plain count.
+ */
+int orc_elems_nested(int k, const uint8_t* adj, const int32_t* order, int64_t n,
+                     const int64_t* rp, const int32_t* col, int64_t root_lo, int64_t root_hi,
+                     int threads, uint64_t* elems_out) {
+    uint64_t c = 0;
+    if (k < 3) return nested_run(k, adj, order, n, rp, col, root_lo, root_hi, threads, &c, elems_out, 0);
+    return nested_run(k, adj, order, n, rp, col, root_lo, root_hi, threads, &c, elems_out, 1);
+}
+
+static int nested_run(int k, const uint8_t* adj, const int32_t* order, int64_t n,
+                      const int64_t* rp, const int32_t* col, int64_t root_lo, int64_t root_hi,
+                      int threads, uint64_t* count_out, uint64_t* elems_out, int elems_only) {
     nplan pl;
     if (!pattern_ok(k, adj) || prepare(&pl, k, adj, order) < 0) return ORC_EINVAL;
     if (root_lo < 0) root_lo = 0;
@@ -533,7 +589,13 @@ int orc_count_nested(int k, const uint8_t* adj, const int32_t* order, int64_t n,
 #pragma omp for schedule(dynamic, 16)
             for (int64_t v = root_lo; v < root_hi; ++v) {
                 emb[0] = (int32_t)v;
-                nested_level(&pl, 1, emb, buf, tmp, &cnt, &el);
+                if (elems_only && k - 2 == 0) {
+                    /* loop 1 is the last loop: its one partial embedding is (e_0) */
+                    int bounded = pl.bp[1] >= 0 && g_mut != MUT_NO_BOUND;
+                    el += (uint64_t)count_below(col + rp[v], rp[v + 1] - rp[v], (int32_t)v, bounded);
+                } else {
+                    nested_level(&pl, 1, emb, buf, tmp, &cnt, &el, elems_only);
+                }
             }
             free(mem);
         }

@@ -28,7 +28,7 @@ EXPORTS = [
     "gz_pattern_named", "gz_plan_create", "gz_plan_create_with_order", "gz_plan_info",
     "gz_plan_schedules", "gz_plan_describe", "gz_plan_destroy", "gz_count", "gz_count_ex", "gz_scratch_bytes",
     "gz_count_batch", "gz_autotune", "gz_server_create", "gz_server_submit", "gz_server_wait",
-    "gz_server_replay", "gz_server_destroy", "gz_last_error", "gz_version",
+    "gz_server_replay", "gz_server_destroy", "gz_last_error", "gz_version", "gz_kernel_launches",
 ]
 
 
@@ -74,6 +74,8 @@ def lib() -> ctypes.CDLL:
     I, I64, S = ctypes.c_int, ctypes.c_int64, ctypes.c_int32
     L.gz_last_error.restype = ctypes.c_char_p
     L.gz_version.restype = ctypes.c_char_p
+    L.gz_kernel_launches.restype = ctypes.c_uint64
+    L.gz_kernel_launches.argtypes = []
     sig = {
         "gz_load_csr": [_P, _P, I64, I64, I, ctypes.c_uint32, _P, ctypes.POINTER(_P)],
         "gz_orient": [_P, _P],
@@ -130,6 +132,11 @@ def _stream(stream) -> int | None:
 
 def version() -> str:
     return lib().gz_version().decode()
+
+
+def kernel_launches() -> int:
+    """CUDA kernels libgz has launched in this process."""
+    return int(lib().gz_kernel_launches())
 
 
 # ------------------------------------------------------------------ patterns

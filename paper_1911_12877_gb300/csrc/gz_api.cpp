@@ -20,6 +20,8 @@ namespace {
 thread_local char g_err[512] = "";
 }
 
+std::atomic<unsigned long long> g_launches{0};
+
 void set_error(const char* fmt, ...) {
     va_list ap;
     va_start(ap, fmt);
@@ -205,6 +207,8 @@ extern "C" {
 const char* gz_last_error(void) { return gz::g_err; }
 const char* gz_version(void) { return "gz-gb300 0.1 (sm_103a)"; }
 
+uint64_t gz_kernel_launches(void) { return g_launches.load(); }
+
 gz_status gz_load_csr(const int64_t* row_ptr, const int32_t* col_idx, int64_t n, int64_t nnz,
                       int device_ptrs, uint32_t flags, void* stream, gz_graph** out) {
     if (!out) { set_error("gz_load_csr: out is NULL"); return GZ_EINVAL; }
@@ -383,7 +387,7 @@ gz_status gz_plan_schedules(int k, const uint8_t* adj, int32_t* orders, int cap,
 gz_status gz_plan_describe(const gz_plan* p, char* buf, int cap) {
     if (!p || !buf || cap <= 0) { set_error("gz_plan_describe: bad arguments"); return GZ_EINVAL; }
     const GzProg& g = p->prog;
-    std::string s = "unit dag=" + std::to_string(g.unit_dag) + "\n";
+    std::string s = "unit dag=" + std::to_string(g.unit_dag) + " flat=" + std::to_string(g.flat) + "\n";
     for (int i = 0; i < g.nops; ++i) {
         const GzOp& o = g.ops[i];
         char line[256];

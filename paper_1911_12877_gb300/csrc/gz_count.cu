@@ -28,6 +28,9 @@ namespace gz {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kStageWords = 1024;                      // per-warp shared staging (int32)
+constexpr int kWarpSmemWords = kStageWords + 32 + 64;  // + lane offsets + 32 list pointers
+constexpr int kHeavy = 8;                              // stream F instead when |N(c)| > 8 |F part|
 
 // Per-query descriptor in device memory.
 struct KQ {
@@ -205,8 +208,164 @@ __device__ __forceinline__ ListRef cand_list(const KQ& q, int d, const WarpState
     return r;
 }
 
-__device__ void process_unit(const KQ& q, int64_t unit, WarpState& ws, int32_t* scratch, int lane,
-                             unsigned long long& acc, int* status) {
+// Per-lane lower bound in a sorted list: number of elements < beta.
+__device__ __forceinline__ int64_t lane_lower_bound(const int32_t* p, int64_t n, int32_t beta) {
+    int64_t lo = 0, len = n;
+    while (len > 0) {
+        int64_t half = len >> 1;
+        if (p[lo + half] < beta) { lo += half + 1; len -= half + 1; }
+        else len = half;
+    }
+    return lo;
+}
+
+// Membership in a sorted array (shared or global memory).
+__device__ __forceinline__ bool in_sorted(const int32_t* A, int64_t n, int32_t x) {
+    int64_t lo = 0, len = n;
+    while (len > 0) {
+        int64_t half = len >> 1;
+        if (A[lo + half] < x) { lo += half + 1; len -= half + 1; }
+        else len = half;
+    }
+    return lo < n && A[lo] == x;
+}
+
+__device__ __forceinline__ bool excluded(uint8_t mask, const WarpState& ws, int32_t x) {
+    bool ex = false;
+    if (mask)
+        for (int j = 0; j < GZ_MAX_K; ++j)
+            if ((mask >> j & 1) && ws.emb[j] == x) ex = true;
+    return ex;
+}
+
+// The last loop, flattened over every candidate c of loop k-2. The one count
+// operation of loop k-2 reads N(c) and otherwise only sets fixed for this call:
+//  shape 1: |F[<b_c] op N(c)[<b_c]| with F fixed (the left operand);
+//  shape 2: |N(c)[<b_c] filtered by fixed right lists|.
+// Lanes stream the concatenation of the lists N(c)[<b_c] (coalesced) and probe
+// F (staged in shared memory when it fits) or the fixed right lists. A shape-1
+// candidate whose list is much longer than its part of F is done the other
+// way round (stream F, binary-search N(c)), so hub lists are never streamed.
+__device__ void last_level_flat(const KQ& q, const GzOp& op, WarpState& ws, ListRef S,
+                                int32_t* scratch, int32_t* sm, int lane, unsigned long long& acc) {
+    const GzProg& P = q.prog;
+    const int t = P.k - 2;
+    const uint8_t cex = P.cand_excl[t];
+    const bool shape2 = P.flat == 2;
+    int32_t* offs = sm + kStageWords;
+    const int32_t** rptr = reinterpret_cast<const int32_t**>(sm + kStageWords + 32);
+    const int32_t* F = nullptr;
+    int64_t nF = 0;
+    const bool sub = !shape2 && op.right_sub[0] != 0;
+    const bool bounded = op.bound_pos >= 0;
+    if (!shape2) {
+        if (op.left_buf >= 0) {
+            F = scratch + q.buf_off[op.left_buf];
+            nF = ws.blen[op.left_buf];
+        } else {
+            ListRef r = adj_list(q, ws.emb[op.left_pos], op.left_dag);
+            F = r.p;
+            nF = r.n;
+        }
+        if (bounded && op.bound_pos != t) nF = warp_lower_bound_rw(F, nF, ws.emb[op.bound_pos], lane);
+        if (nF <= kStageWords) {
+            for (int64_t i = lane; i < nF; i += 32) sm[i] = F[i];
+            __syncwarp();
+            F = sm;
+        }
+    }
+    const int sdag = shape2 ? op.left_dag : op.right_dag[0];
+    // e_t is the candidate c itself and is not stored in ws.emb on this path. A
+    // streamed or matched x lies in N(c), so x != c; only the subtraction's
+    // exclusion count below has to consider c.
+    const uint8_t xm = op.excl_mask & (uint8_t)~(1u << t);
+    const bool excl_self = (op.excl_mask >> t) & 1;
+    for (int64_t base = 0; base < S.n; base += 32) {
+        const int64_t idx = base + lane;
+        bool valid = idx < S.n;
+        const int32_t c = valid ? S.p[idx] : 0;
+        if (valid && excluded(cex, ws, c)) valid = false;
+        const int32_t* R = nullptr;
+        int64_t m = 0, Lc = 0;
+        int32_t beta = INT_MAX;
+        if (valid) {
+            ListRef r = adj_list(q, c, sdag);
+            R = r.p;
+            m = r.n;
+            if (bounded) beta = op.bound_pos == t ? c : ws.emb[op.bound_pos];
+            if (bounded && sdag != 2) m = lane_lower_bound(R, m, beta);
+            if (!shape2) {
+                if (bounded && op.bound_pos == t) Lc = op.left_iter ? idx : lane_lower_bound(F, nF, c);
+                else Lc = nF;
+                if (Lc == 0) valid = false;  // empty left part: contributes nothing
+            }
+        }
+        bool heavy = valid && !shape2 && m > kHeavy * Lc + 32;
+        if (valid && sub) {
+            acc += (unsigned long long)Lc;  // |F part|, matches are subtracted below
+            for (int j = 0; j < GZ_MAX_K; ++j)
+                if ((xm >> j & 1) || (j == t && excl_self)) {
+                    const int32_t e = j == t ? c : ws.emb[j];
+                    if (e < beta && in_sorted(F, Lc, e) && !in_sorted(R, m, e)) acc -= 1ull;
+                }
+        }
+        // flattened streaming of the light candidates' lists
+        int64_t ml = (valid && !heavy) ? m : 0;
+        int64_t incl = ml;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int64_t total = __shfl_sync(kFull, incl, 31);
+        __syncwarp();
+        offs[lane] = (int32_t)incl;
+        rptr[lane] = R;
+        __syncwarp();
+        for (int64_t f = lane; f < total; f += 32) {
+            int lo = 0, hi = 31;  // first lane whose inclusive offset exceeds f
+            while (lo < hi) {
+                int mid = (lo + hi) >> 1;
+                if (offs[mid] > f) hi = mid; else lo = mid + 1;
+            }
+            const int64_t start = lo ? offs[lo - 1] : 0;
+            const int32_t x = __ldg(rptr[lo] + (f - start));
+            if (shape2) {
+                bool keep = true;
+                for (int r = 0; r < op.nright && keep; ++r) {
+                    ListRef rl = adj_list(q, ws.emb[op.right_pos[r]], op.right_dag[r]);
+                    keep = in_sorted(rl.p, rl.n, x) != (op.right_sub[r] != 0);
+                }
+                if (keep && !excluded(xm, ws, x)) acc += 1ull;
+            } else {
+                const bool found = in_sorted(F, nF, x);
+                if (!sub) acc += (found && !excluded(xm, ws, x)) ? 1ull : 0ull;
+                else acc -= found ? 1ull : 0ull;
+            }
+        }
+        __syncwarp();
+        // heavy candidates one at a time: stream F[0, Lc), probe N(c)[<b_c]
+        unsigned hm = __ballot_sync(kFull, heavy);
+        while (hm) {
+            const int h = __ffs(hm) - 1;
+            hm &= hm - 1;
+            const int32_t* Rh = reinterpret_cast<const int32_t*>(
+                __shfl_sync(kFull, reinterpret_cast<unsigned long long>(R), h));
+            const int64_t mh = __shfl_sync(kFull, m, h);
+            const int64_t Lh = __shfl_sync(kFull, Lc, h);
+            for (int64_t i = lane; i < Lh; i += 32) {
+                const int32_t x = F[i];
+                const bool found = contains(Rh, (int)mh, x);
+                if (!sub) acc += (found && !excluded(xm, ws, x)) ? 1ull : 0ull;
+                else acc -= found ? 1ull : 0ull;
+            }
+        }
+    }
+    __syncwarp();
+}
+
+__device__ void process_unit(const KQ& q, int64_t unit, WarpState& ws, int32_t* scratch,
+                             int32_t* sm, int lane, unsigned long long& acc, int* status) {
     const GzProg& P = q.prog;
     const int k = P.k;
     const int32_t e0 = q.usrc[unit];
@@ -220,7 +379,14 @@ __device__ void process_unit(const KQ& q, int64_t unit, WarpState& ws, int32_t* 
     }
     run_level(q, 1, ws, scratch, lane, acc, status);
     if (k == 3) return;
-    // explicit DFS over loops 2..k-2
+    const bool flat = P.flat != 0;
+    if (k == 4 && flat) {
+        last_level_flat(q, P.ops[P.level_begin[2]], ws, cand_list(q, 2, ws, scratch, lane), scratch, sm,
+                        lane, acc);
+        return;
+    }
+    // explicit DFS over loops 2..k-2 (2..k-3 when the last loop is flattened)
+    const int dmax = flat ? k - 3 : k - 2;
     const int32_t* cp[GZ_MAX_K];
     int64_t cn[GZ_MAX_K], it[GZ_MAX_K];
     int d = 2;
@@ -241,10 +407,13 @@ __device__ void process_unit(const KQ& q, int64_t unit, WarpState& ws, int32_t* 
         ws.emb[d] = c;
         ws.itp[d] = pos;
         run_level(q, d, ws, scratch, lane, acc, status);
-        if (d < k - 2) {
+        if (d < dmax) {
             ++d;
             ListRef r = cand_list(q, d, ws, scratch, lane);
             cp[d] = r.p; cn[d] = r.n; it[d] = 0;
+        } else if (flat) {
+            last_level_flat(q, P.ops[P.level_begin[k - 2]], ws, cand_list(q, k - 2, ws, scratch, lane),
+                            scratch, sm, lane, acc);
         }
     }
 }
@@ -263,9 +432,11 @@ __global__ void __launch_bounds__(512) k_enumerate(const KQ* __restrict__ qs, in
                                                    int* __restrict__ status,
                                                    int32_t* __restrict__ scratch,
                                                    int64_t words_per_warp) {
+    extern __shared__ int32_t smem[];
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int32_t* my = scratch + gwarp * words_per_warp;
+    int32_t* sm = smem + (threadIdx.x >> 5) * kWarpSmemWords;
     WarpState ws;
     unsigned long long acc = 0;
     int cur = -1;
@@ -291,7 +462,7 @@ __global__ void __launch_bounds__(512) k_enumerate(const KQ* __restrict__ qs, in
                 cur = lo;
             }
             const KQ& q = qs[cur];
-            process_unit(q, q.unit_lo + (u - q.unit_begin), ws, my, lane, acc, status);
+            process_unit(q, q.unit_lo + (u - q.unit_begin), ws, my, sm, lane, acc, status);
         }
     }
     if (cur >= 0) {
@@ -315,7 +486,14 @@ int resident_warps(const LaunchCfg& cfg) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate, cfg.block_warps * 32, 0);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_enumerate, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             16 * kWarpSmemWords * 4);
+        attr = true;
+    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate, cfg.block_warps * 32,
+                                                  cfg.block_warps * kWarpSmemWords * 4);
     if (per_sm < 1) per_sm = 1;
     int blocks = cfg.blocks > 0 ? cfg.blocks : sms * per_sm;
     return blocks * cfg.block_warps;
@@ -369,9 +547,10 @@ gz_status count_launch(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream
     if (e == cudaSuccess) e = cudaMemsetAsync(work, 0, 16, s);
     if (e == cudaSuccess) {
         const int blocks = warps / cfg.block_warps;
-        k_enumerate<<<blocks, cfg.block_warps * 32, 0, s>>>(
+        k_enumerate<<<blocks, cfg.block_warps * 32, cfg.block_warps * kWarpSmemWords * 4, s>>>(
             d, nq, total, cfg.chunk > 0 ? cfg.chunk : 1, work, d_counts, d_status,
             reinterpret_cast<int32_t*>(scratch), (int64_t)words);
+        GZ_COUNT_LAUNCH();
         e = cudaGetLastError();
     }
     cudaFreeAsync(d, s);

@@ -91,15 +91,18 @@ cudaError_t exclusive_scan(const int64_t* in, int64_t* out, int64_t n, cudaStrea
     int64_t tiles = (n + kScanTile - 1) / kScanTile;
     if (tiles == 1) {
         scan_tiles<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
+        GZ_COUNT_LAUNCH();
         return cudaGetLastError();
     }
     int64_t* sums = nullptr;
     cudaError_t e = cudaMallocAsync(&sums, sizeof(int64_t) * tiles, s);
     if (e != cudaSuccess) return e;
     scan_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, sums);
+    GZ_COUNT_LAUNCH();
     e = exclusive_scan(sums, sums, tiles, s);
     if (e == cudaSuccess) {
         add_tile_offsets<<<(unsigned)tiles, kScanThreads, 0, s>>>(out, n, sums);
+        GZ_COUNT_LAUNCH();
         e = cudaGetLastError();
     }
     cudaFreeAsync(sums, s);
@@ -193,9 +196,11 @@ cudaError_t radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t*
     for (int p = 0; p < passes && e == cudaSuccess; ++p) {
         int shift = 8 * p;
         radix_hist<<<(unsigned)ntiles, kThreads, 0, s>>>(k0, n, shift, hist, ntiles);
+        GZ_COUNT_LAUNCH();
         e = exclusive_scan(hist, hist, 256 * ntiles, s);
         if (e != cudaSuccess) break;
         radix_scatter<<<(unsigned)ntiles, kThreads, 0, s>>>(k0, v0, k1, v1, n, shift, hist, ntiles);
+        GZ_COUNT_LAUNCH();
         e = cudaGetLastError();
         std::swap(k0, k1);
         std::swap(v0, v1);
@@ -378,7 +383,10 @@ gz_status max_degree(const int64_t* rp, int64_t n, int64_t* out, cudaStream_t s)
     cudaError_t e = cudaMallocAsync(&d, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
     cudaMemsetAsync(d, 0, sizeof(unsigned long long), s);
-    if (n > 0) k_degrees<<<grid_for(n, kThreads), kThreads, 0, s>>>(rp, n, nullptr, d);
+    if (n > 0) {
+        k_degrees<<<grid_for(n, kThreads), kThreads, 0, s>>>(rp, n, nullptr, d);
+        GZ_COUNT_LAUNCH();
+    }
     unsigned long long h = 0;
     e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
     cudaFreeAsync(d, s);
@@ -408,6 +416,7 @@ gz_status validate_csr(const int64_t* rp, const int32_t* col, int64_t n, int64_t
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
     cudaMemsetAsync(err, 0, sizeof(unsigned long long) * 5, s);
     k_validate<<<warp_grid(n), kThreads, 0, s>>>(rp, col, n, nnz, symmetric ? 1 : 0, err);
+    GZ_COUNT_LAUNCH();
     unsigned long long h[5];
     e = cudaMemcpyAsync(h, err, sizeof(h), cudaMemcpyDeviceToHost, s);
     cudaFreeAsync(err, s);
@@ -435,7 +444,10 @@ gz_status build_dag(gz_graph* g, GzView* v, cudaStream_t s) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
     cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s);
     cudaMemsetAsync(v->dag_rp + n, 0, sizeof(int64_t), s);
-    if (n > 0) k_split<<<warp_grid(n), kThreads, 0, s>>>(v->rp, v->col, n, v->dag_rp, mx);
+    if (n > 0) {
+        k_split<<<warp_grid(n), kThreads, 0, s>>>(v->rp, v->col, n, v->dag_rp, mx);
+        GZ_COUNT_LAUNCH();
+    }
     e = exclusive_scan(v->dag_rp, v->dag_rp, n + 1, s);
     int64_t dnnz = 0;
     unsigned long long hmx = 0;
@@ -449,7 +461,10 @@ gz_status build_dag(gz_graph* g, GzView* v, cudaStream_t s) {
     e = cudaMalloc(&v->dag_col, bytes);
     if (e == cudaSuccess) e = cudaMalloc(&v->dag_src, bytes);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc dag");
-    if (n > 0) k_dag_fill<<<warp_grid(n), kThreads, 0, s>>>(v->rp, v->col, v->dag_rp, n, v->dag_col, v->dag_src);
+    if (n > 0) {
+        k_dag_fill<<<warp_grid(n), kThreads, 0, s>>>(v->rp, v->col, v->dag_rp, n, v->dag_col, v->dag_src);
+        GZ_COUNT_LAUNCH();
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "build dag: fill");
     v->dag_nnz = dnnz;
@@ -462,7 +477,10 @@ gz_status build_src(gz_graph* g, GzView* v, cudaStream_t s) {
     if (v->src) return GZ_OK;
     cudaError_t e = cudaMalloc(&v->src, sizeof(int32_t) * (size_t)(g->nnz > 0 ? g->nnz : 1));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc src");
-    if (g->n > 0) k_src<<<warp_grid(g->n), kThreads, 0, s>>>(v->rp, g->n, v->src);
+    if (g->n > 0) {
+        k_src<<<warp_grid(g->n), kThreads, 0, s>>>(v->rp, g->n, v->src);
+        GZ_COUNT_LAUNCH();
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "build src");
     return GZ_OK;
@@ -505,12 +523,15 @@ gz_status orient(gz_graph* g, cudaStream_t s) {
         cudaMemsetAsync(bad, 0, sizeof(unsigned long long), s);
         // 1. degrees -> rank keys (max_deg - deg), stable sort by key
         k_degrees<<<grid_for(n, kThreads), kThreads, 0, s>>>(g->orig.rp, n, deg, bad);
+        GZ_COUNT_LAUNCH();
         cudaMemsetAsync(bad, 0, sizeof(unsigned long long), s);
         k_rank_keys<<<grid_for(n, kThreads), kThreads, 0, s>>>(deg, n, g->max_deg, k0, v0);
+        GZ_COUNT_LAUNCH();
         e = radix_sort_pairs(k0, v0, k1, v1, n, bits_for((uint64_t)g->max_deg), s);
         if (e != cudaSuccess) { st = cuda_fail(e, "gz_orient: rank sort"); goto done; }
         // 2. new ids and new row pointers (v0 = order: old id per rank)
         k_new_ids<<<grid_for(n, kThreads), kThreads, 0, s>>>(v0, deg, n, g->new_id, ndeg);
+        GZ_COUNT_LAUNCH();
         cudaMemsetAsync(ndeg + n, 0, sizeof(int64_t), s);
         e = exclusive_scan(ndeg, o.rp, n + 1, s);
         if (e != cudaSuccess) { st = cuda_fail(e, "gz_orient: row scan"); goto done; }
@@ -526,10 +547,12 @@ gz_status orient(gz_graph* g, cudaStream_t s) {
         if (e != cudaSuccess) { st = cuda_fail(e, "gz_orient: order copy"); goto done; }
         k_relabel_rows<<<warp_grid(n), kThreads, 0, s>>>(g->orig.rp, g->orig.col, order_copy,
                                                         g->new_id, o.rp, n, k0, v0);
+        GZ_COUNT_LAUNCH();
         cudaFreeAsync(order_copy, s);
         e = radix_sort_pairs(k0, v0, k1, v1, nnz, bits_for((uint64_t)(n - 1)), s);
         if (e != cudaSuccess) { st = cuda_fail(e, "gz_orient: edge sort"); goto done; }
         k_check_segments<<<warp_grid(n), kThreads, 0, s>>>(k0, o.rp, n, bad);
+        GZ_COUNT_LAUNCH();
         e = cudaMemcpyAsync(o.col, v0, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, s);
         unsigned long long hbad = 0;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, s);

@@ -2,6 +2,7 @@
 // of libgz. Not part of the public C ABI (include/gz.h is).
 #pragma once
 #include <stdint.h>
+#include <atomic>
 #include <cuda_runtime.h>
 
 #include "../../include/gz.h"
@@ -35,6 +36,7 @@ struct GzProg {
     int32_t nops;
     int32_t nbuf;
     int32_t unit_dag;                 // level-1 candidates are out-lists (bp[1] == 0)
+    int32_t flat;                     // last loop flattened: 1 fixed left operand, 2 left = N(e_{k-2}), 0 no
     GzOp ops[GZ_MAXOPS];
     int8_t level_begin[GZ_MAX_K];     // ops[level_begin[t] .. level_end[t]) run at loop t
     int8_t level_end[GZ_MAX_K];
@@ -89,6 +91,10 @@ struct gz_graph {
 };
 
 namespace gz {
+
+// Kernels this library has launched in this process (for launch accounting).
+extern std::atomic<unsigned long long> g_launches;
+#define GZ_COUNT_LAUNCH() (::gz::g_launches.fetch_add(1, std::memory_order_relaxed))
 
 void set_error(const char* fmt, ...);
 gz_status cuda_fail(cudaError_t e, const char* what);

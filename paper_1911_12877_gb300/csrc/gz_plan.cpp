@@ -262,6 +262,20 @@ struct Compiler {
             }
             prog.level_end[t] = (int8_t)prog.nops;
         }
+        // shape of loop k-2's single count operation (see the kernel's flattened last loop)
+        prog.flat = 0;
+        if (k >= 4 && prog.level_end[k - 2] - prog.level_begin[k - 2] == 1) {
+            const GzOp& op = prog.ops[prog.level_begin[k - 2]];
+            if (op.dst < 0) {
+                if (op.left_buf < 0 && op.left_pos == k - 2) {
+                    bool fixed = true;
+                    for (int r = 0; r < op.nright; ++r) fixed = fixed && op.right_pos[r] < k - 2;
+                    if (fixed) prog.flat = 2;
+                } else if (op.nright == 1 && op.right_pos[0] == k - 2) {
+                    prog.flat = 1;
+                }
+            }
+        }
         out = prog;
         return true;
     }

@@ -252,6 +252,17 @@ def test_elems_match_brute_definition(name):
         assert O.count_nested(a, s, g)[1] == O.elems_brute(a, s, g)
 
 
+@pytest.mark.parametrize("name", ["edge", "wedge", "triangle", "c4", "paw", "house", "k4", "k5",
+                                  "chordal5", "asym6"])
+def test_elems_without_last_loop_equal_plain_elems(name):
+    a = adjacency(name)
+    for g in [S.random_small(12, 0.5, 3), S.rmat(8, 8, 4)]:
+        for og in [g, O.reindex(g)[0]]:
+            for s in O.distinct_schedules(a)[:4]:
+                assert O.elems_nested(a, s, og) == O.count_nested(a, s, og)[1]
+                assert O.elems_nested(a, s, og, 3, 40) == O.count_nested(a, s, og, 3, 40)[1]
+
+
 def test_root_ranges_partition_the_count():
     a = adjacency("diamond")
     g = S.random_small(40, 0.3, 9)

@@ -23,7 +23,7 @@ def test_library_exports_every_declared_symbol():
     import re
     import os
     hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "gz.h")).read()
-    declared = set(re.findall(r"^(?:gz_status|void|const char\*)\s+(gz_\w+)\(", hdr, re.M))
+    declared = set(re.findall(r"^(?:gz_status|void|const char\*|uint64_t)\s+(gz_\w+)\(", hdr, re.M))
     assert declared == set(gz.EXPORTS)
     L = gz.lib()
     for name in declared:
@@ -73,6 +73,7 @@ def parse(desc):
         f = line.split()
         if f[0] == "unit":
             prog["unit_dag"] = int(f[1].split("=")[1])
+            prog["flat"] = int(f[2].split("=")[1])
         elif f[0] == "op":
             kv = dict(x.split("=", 1) for x in f[1:])
             op = {k: int(v) for k, v in kv.items() if k != "rights"}
@@ -89,8 +90,10 @@ def parse(desc):
 class Interp:
     """Runs a compiled program the way the kernel does, one root edge at a time."""
 
-    def __init__(self, prog, k, g):
+    def __init__(self, prog, k, g, flat=False, heavy=None):
         self.p, self.k, self.g = prog, k, g
+        self.flat = flat and prog["flat"] != 0 and k >= 4
+        self.heavy = heavy  # None: the kernel's rule; True / False: force one path
         self.out = {v: [int(u) for u in g.neighbors(v) if u < v] for v in range(g.n)}
         self.full = {v: [int(u) for u in g.neighbors(v)] for v in range(g.n)}
 
@@ -112,7 +115,65 @@ class Interp:
                     continue
                 total += self.level(1, emb, itp, bufs)
                 if k > 3:
-                    total += self.dfs(2, emb, itp, bufs)
+                    if self.flat and k == 4:
+                        total += self.flat_last(emb, bufs)
+                    else:
+                        total += self.dfs(2, emb, itp, bufs)
+        return total
+
+    def flat_last(self, emb, bufs):
+        """The kernel's flattened last loop over the candidates c of loop k-2."""
+        k, p = self.k, self.p
+        t = k - 2
+        op = [o for o in p["ops"] if o["level"] == t][0]
+        S = self.cands(t, emb, bufs)
+        cex = p["cand"][t]["excl"] if t >= 2 else 0
+        shape2 = p["flat"] == 2
+        xm = op["excl"] & ~(1 << t)
+        excl_self = op["excl"] >> t & 1
+        bnd = op["bound"]
+        if shape2:
+            sdag = op["left_dag"]
+        else:
+            sdag = op["rights"][0][2]
+            sub = bool(op["rights"][0][1])
+            F = list(bufs[op["left_buf"]]) if op["left_buf"] >= 0 else \
+                self.lst(emb[op["left_pos"]], op["left_dag"])
+            if bnd >= 0 and bnd != t:
+                F = [x for x in F if x < emb[bnd]]
+        ex = lambda x: any((xm >> j & 1) and emb[j] == x for j in range(k))
+        total = 0
+        for idx, c in enumerate(S):
+            if any((cex >> j & 1) and emb[j] == c for j in range(t)):
+                continue
+            beta = None if bnd < 0 else (c if bnd == t else emb[bnd])
+            R = self.lst(c, sdag)
+            if beta is not None and sdag != 2:
+                R = [x for x in R if x < beta]
+            if shape2:
+                for x in R:
+                    keep = all((x in set(self.lst(emb[pos], dag))) != bool(sb)
+                               for pos, sb, dag in op["rights"])
+                    total += keep and not ex(x)
+                continue
+            if bnd == t:
+                Lc = idx if op["left_iter"] else sum(1 for x in F if x < c)
+            else:
+                Lc = len(F)
+            if Lc == 0:
+                continue
+            heavy = len(R) > 8 * Lc + 32 if self.heavy is None else self.heavy
+            if sub:
+                total += Lc
+                for j in range(k):
+                    if (xm >> j & 1) or (j == t and excl_self):
+                        e = c if j == t else emb[j]
+                        if (beta is None or e < beta) and e in F[:Lc] and e not in R:
+                            total -= 1
+            stream, probe = (F[:Lc], set(R)) if heavy else (R, set(F))
+            for x in stream:
+                found = x in probe
+                total += (found and not ex(x)) if not sub else -found
         return total
 
     def level(self, t, emb, itp, bufs):
@@ -166,7 +227,9 @@ class Interp:
                 continue
             emb[d], itp[d] = x, pos
             c += self.level(d, emb, itp, bufs)
-            if d < self.k - 2:
+            if self.flat and d == self.k - 3:
+                c += self.flat_last(emb, dict(bufs))
+            elif d < self.k - 2:
                 c += self.dfs(d + 1, emb, itp, dict(bufs))
         return c
 
@@ -180,8 +243,9 @@ def test_compiled_program_counts_every_schedule(name):
         go, _ = O.reindex(g)
         for s in O.distinct_schedules(a)[:10]:
             prog = parse(gz.Plan(a, order=s).describe())
-            assert Interp(prog, len(a), g).run() == want, (name, s)
-            assert Interp(prog, len(a), go).run() == want, (name, s, "oriented")
+            for flat, heavy in ((False, None), (True, None), (True, True), (True, False)):
+                assert Interp(prog, len(a), g, flat, heavy).run() == want, (name, s, flat, heavy)
+                assert Interp(prog, len(a), go, flat, heavy).run() == want, (name, s, flat, heavy, "or")
 
 
 def test_clique_program_is_chain_of_out_list_intersections():
