@@ -142,7 +142,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("gz_count.cu", "gz_internal.h"):
+    for f in ("gz_clique.cu", "gz_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_1911_12877_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -263,11 +263,16 @@ def run_clique(args, dist, world, rank, local):
     peak, peak_kind = measured_peaks()
     k5_s = statistics.mean(k5_ms) / 1e3
     achieved = 4.0 * e_k5 / k5_s / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_enumerate (K5)", "achieved": round(achieved, 1),
-                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": profiled_traffic("k_enumerate_k5_rmat20.json"),
+    traffic = profiled_traffic("k_clique_big_k5_rmat20.json")
+    roofline = {"bound": "hbm", "kernel": "k_clique_small<5> + k_clique_big<5> (K5 count)",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_kind": peak_kind, "kernel_ms": round(k5_s * 1e3, 3),
-                "algorithmic_bytes": 4 * e_k5}
+                "algorithmic_bytes": 4 * e_k5,
+                "dram_frac": (round(traffic / k5_s / 1e9 / peak, 6) if traffic else None),
+                "note": "algorithmic bytes = 4 x E, E = list elements the paper's unshared bounded "
+                        "scans consume; the bitset kernel reuses loop-invariant sets on chip, so "
+                        "4E/t exceeds the HBM peak while its measured DRAM traffic is ~0.3% of 4E"}
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timing
     e2e = None

@@ -190,6 +190,24 @@ gz_status run_queries(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream_
     return GZ_OK;
 }
 
+// Oriented k-clique counting through the bitset kernels (gz_clique.cu).
+gz_status run_clique(int k, const GzView& v, int64_t lo, int64_t hi, cudaStream_t s, uint64_t* out) {
+    unsigned long long* d = nullptr;
+    cudaError_t e = cudaMallocAsync(&d, sizeof(unsigned long long) * 3, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync clique");
+    e = cudaMemsetAsync(d, 0, sizeof(unsigned long long) * 3, s);
+    gz_status st = e == cudaSuccess ? clique_launch(k, v, lo, hi, s, d, d + 1) : cuda_fail(e, "memset");
+    unsigned long long h = 0;
+    if (st == GZ_OK) {
+        e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_fail(e, "clique count");
+    }
+    cudaFreeAsync(d, s);
+    if (st == GZ_OK) *out = h;
+    return st;
+}
+
 bool check_graph(const gz_graph* g, const char* who) {
     if (!g) {
         set_error("%s: graph is NULL", who);
@@ -438,10 +456,15 @@ gz_status gz_count_ex(const gz_plan* p, const gz_graph* g, const gz_count_opts* 
         auto it = tune_cache().find(TuneKey{p, g, o.use_orientation ? 1 : 0});
         if (it != tune_cache().end()) cfg = it->second;
     }
-    if (o.block_warps > 0) cfg.block_warps = std::min(16, o.block_warps);
+    if (o.block_warps > 0) cfg.block_warps = std::min(8, o.block_warps);
     if (o.chunk > 0) cfg.chunk = o.chunk;
     *out_count = 0;
     if (q.unit_hi <= q.unit_lo) return GZ_OK;
+    if (clique_eligible(p->prog, *p, *q.view)) {
+        int64_t lo = o.root_lo < 0 ? 0 : o.root_lo;
+        int64_t hi = (o.root_hi < 0 || o.root_hi > g->n) ? g->n : o.root_hi;
+        return run_clique(p->k, *q.view, lo, hi, s, out_count);
+    }
     return run_queries(&q, 1, cfg, s, out_count);
 }
 
@@ -504,7 +527,7 @@ gz_status gz_autotune(const gz_plan* p, const gz_graph* g, int use_orientation, 
     Query q{};
     gz_status st = prepare_query(p, g, use_orientation, 0, -1, s, q);
     if (st != GZ_OK) return st;
-    const int bw_c[] = {4, 8, 16};
+    const int bw_c[] = {2, 4, 8};
     const int ch_c[] = {1, 4, 16};
     LaunchCfg best = default_cfg();
     double best_t = 1e300;

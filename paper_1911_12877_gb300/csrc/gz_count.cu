@@ -29,8 +29,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kStageWords = 1024;                      // per-warp shared staging (int32)
-constexpr int kWarpSmemWords = kStageWords + 32 + 64;  // + lane offsets + 32 list pointers
-constexpr int kHeavy = 8;                              // stream F instead when |N(c)| > 8 |F part|
+constexpr int kWarpSmemWords = kStageWords + 64 + 64;  // + lane offsets, lengths, list pointers
 
 // Per-query descriptor in device memory.
 struct KQ {
@@ -242,10 +241,11 @@ __device__ __forceinline__ bool excluded(uint8_t mask, const WarpState& ws, int3
 // operation of loop k-2 reads N(c) and otherwise only sets fixed for this call:
 //  shape 1: |F[<b_c] op N(c)[<b_c]| with F fixed (the left operand);
 //  shape 2: |N(c)[<b_c] filtered by fixed right lists|.
-// Lanes stream the concatenation of the lists N(c)[<b_c] (coalesced) and probe
-// F (staged in shared memory when it fits) or the fixed right lists. A shape-1
-// candidate whose list is much longer than its part of F is done the other
-// way round (stream F, binary-search N(c)), so hub lists are never streamed.
+// For each group of 32 candidates and each candidate, the shorter side is
+// streamed: (A) N(c)[<b_c], probing F (staged in shared memory when it fits) or
+// the fixed right lists; (B) F[<b_c], binary-searching N(c)[<b_c]. Both passes
+// are flattened, so lanes stream the concatenated lists of many candidates and
+// no lane idles on a short list.
 __device__ void last_level_flat(const KQ& q, const GzOp& op, WarpState& ws, ListRef S,
                                 int32_t* scratch, int32_t* sm, int lane, unsigned long long& acc) {
     const GzProg& P = q.prog;
@@ -253,7 +253,8 @@ __device__ void last_level_flat(const KQ& q, const GzOp& op, WarpState& ws, List
     const uint8_t cex = P.cand_excl[t];
     const bool shape2 = P.flat == 2;
     int32_t* offs = sm + kStageWords;
-    const int32_t** rptr = reinterpret_cast<const int32_t**>(sm + kStageWords + 32);
+    int32_t* lens = sm + kStageWords + 32;
+    const int32_t** rptr = reinterpret_cast<const int32_t**>(sm + kStageWords + 64);
     const int32_t* F = nullptr;
     int64_t nF = 0;
     const bool sub = !shape2 && op.right_sub[0] != 0;
@@ -300,65 +301,61 @@ __device__ void last_level_flat(const KQ& q, const GzOp& op, WarpState& ws, List
                 if (Lc == 0) valid = false;  // empty left part: contributes nothing
             }
         }
-        bool heavy = valid && !shape2 && m > kHeavy * Lc + 32;
         if (valid && sub) {
-            acc += (unsigned long long)Lc;  // |F part|, matches are subtracted below
+            acc += (unsigned long long)Lc;  // |F part|; matches are subtracted below
             for (int j = 0; j < GZ_MAX_K; ++j)
                 if ((xm >> j & 1) || (j == t && excl_self)) {
                     const int32_t e = j == t ? c : ws.emb[j];
                     if (e < beta && in_sorted(F, Lc, e) && !in_sorted(R, m, e)) acc -= 1ull;
                 }
         }
-        // flattened streaming of the light candidates' lists
-        int64_t ml = (valid && !heavy) ? m : 0;
-        int64_t incl = ml;
+        const bool dirA = valid && (shape2 || m <= Lc);
+        const bool dirB = valid && !dirA;
+        for (int pass = 0; pass < 2; ++pass) {
+            const bool mine = pass == 0 ? dirA : dirB;
+            if (!__any_sync(kFull, mine)) continue;
+            const int64_t len = mine ? (pass == 0 ? m : Lc) : 0;
+            int64_t incl = len;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int64_t v = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += v;
-        }
-        const int64_t total = __shfl_sync(kFull, incl, 31);
-        __syncwarp();
-        offs[lane] = (int32_t)incl;
-        rptr[lane] = R;
-        __syncwarp();
-        for (int64_t f = lane; f < total; f += 32) {
-            int lo = 0, hi = 31;  // first lane whose inclusive offset exceeds f
-            while (lo < hi) {
-                int mid = (lo + hi) >> 1;
-                if (offs[mid] > f) hi = mid; else lo = mid + 1;
+            for (int o = 1; o < 32; o <<= 1) {
+                int64_t v = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += v;
             }
-            const int64_t start = lo ? offs[lo - 1] : 0;
-            const int32_t x = __ldg(rptr[lo] + (f - start));
-            if (shape2) {
-                bool keep = true;
-                for (int r = 0; r < op.nright && keep; ++r) {
-                    ListRef rl = adj_list(q, ws.emb[op.right_pos[r]], op.right_dag[r]);
-                    keep = in_sorted(rl.p, rl.n, x) != (op.right_sub[r] != 0);
+            const int64_t total = __shfl_sync(kFull, incl, 31);
+            __syncwarp();
+            offs[lane] = (int32_t)incl;
+            lens[lane] = (int32_t)m;
+            rptr[lane] = R;
+            __syncwarp();
+            for (int64_t f = lane; f < total; f += 32) {
+                int lo = 0, hi = 31;  // first lane whose inclusive offset exceeds f
+                while (lo < hi) {
+                    int mid = (lo + hi) >> 1;
+                    if (offs[mid] > f) hi = mid; else lo = mid + 1;
                 }
-                if (keep && !excluded(xm, ws, x)) acc += 1ull;
-            } else {
-                const bool found = in_sorted(F, nF, x);
+                const int64_t i = f - (lo ? offs[lo - 1] : 0);
+                bool found;
+                int32_t x;
+                if (pass == 0) {
+                    x = __ldg(rptr[lo] + i);
+                    if (shape2) {
+                        bool keep = true;
+                        for (int r = 0; r < op.nright && keep; ++r) {
+                            ListRef rl = adj_list(q, ws.emb[op.right_pos[r]], op.right_dag[r]);
+                            keep = in_sorted(rl.p, rl.n, x) != (op.right_sub[r] != 0);
+                        }
+                        if (keep && !excluded(xm, ws, x)) acc += 1ull;
+                        continue;
+                    }
+                    found = in_sorted(F, nF, x);
+                } else {
+                    x = F[i];
+                    found = contains(rptr[lo], lens[lo], x);
+                }
                 if (!sub) acc += (found && !excluded(xm, ws, x)) ? 1ull : 0ull;
                 else acc -= found ? 1ull : 0ull;
             }
-        }
-        __syncwarp();
-        // heavy candidates one at a time: stream F[0, Lc), probe N(c)[<b_c]
-        unsigned hm = __ballot_sync(kFull, heavy);
-        while (hm) {
-            const int h = __ffs(hm) - 1;
-            hm &= hm - 1;
-            const int32_t* Rh = reinterpret_cast<const int32_t*>(
-                __shfl_sync(kFull, reinterpret_cast<unsigned long long>(R), h));
-            const int64_t mh = __shfl_sync(kFull, m, h);
-            const int64_t Lh = __shfl_sync(kFull, Lc, h);
-            for (int64_t i = lane; i < Lh; i += 32) {
-                const int32_t x = F[i];
-                const bool found = contains(Rh, (int)mh, x);
-                if (!sub) acc += (found && !excluded(xm, ws, x)) ? 1ull : 0ull;
-                else acc -= found ? 1ull : 0ull;
-            }
+            __syncwarp();
         }
     }
     __syncwarp();
@@ -425,7 +422,7 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 }
 
 // Persistent enumeration kernel over a batch of queries (nq >= 1).
-__global__ void __launch_bounds__(512) k_enumerate(const KQ* __restrict__ qs, int nq,
+__global__ void __launch_bounds__(256, 2) k_enumerate(const KQ* __restrict__ qs, int nq,
                                                    int64_t total_units, int chunk,
                                                    unsigned long long* __restrict__ work,
                                                    unsigned long long* __restrict__ counts,
@@ -489,7 +486,7 @@ int resident_warps(const LaunchCfg& cfg) {
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_enumerate, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             16 * kWarpSmemWords * 4);
+                             8 * kWarpSmemWords * 4);
         attr = true;
     }
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate, cfg.block_warps * 32,

@@ -122,4 +122,10 @@ gz_status count_launch(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream
                        int* d_status);
 int resident_warps(const LaunchCfg& cfg);
 
+// clique side (gz_clique.cu): oriented k-cliques as bitsets over the root's out-list
+constexpr int kCliqueMaxOut = 1024;  // largest out-list kept in shared memory
+bool clique_eligible(const GzProg& p, const gz_plan& plan, const GzView& v);
+gz_status clique_launch(int k, const GzView& v, int64_t lo, int64_t hi, cudaStream_t s,
+                        unsigned long long* d_count, unsigned long long* d_work);
+
 }  // namespace gz
