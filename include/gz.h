@@ -184,6 +184,33 @@ typedef struct {
 gz_status gz_count_ex(const gz_plan* p, const gz_graph* g, const gz_count_opts* opts,
                       void* stream, uint64_t* out_count);
 
+/* Size of the static scratch array that gz_count_noalloc works in (32 MiB). */
+#define GZ_NOALLOC_SCRATCH_BYTES (32ull << 20)
+
+/*
+ * gz_count for callers that cannot allocate device memory when they count:
+ * code that runs while a CUDA stream is being captured into a graph, real-time
+ * loops that forbid allocator calls after start-up, or hosts whose own memory
+ * manager owns the whole device. The paper has no counterpart.
+ *
+ * Counts the plan's pattern over the whole graph (use_orientation as in
+ * gz_count) with the general enumeration kernel and writes the exact count to
+ * *out_count (host). It calls no cudaMalloc, cudaFree or other allocating
+ * routine: its counters and set-operation scratch live in a static device
+ * array of 256 + GZ_NOALLOC_SCRATCH_BYTES bytes that every GPU using the
+ * library holds until the process exits; a plan whose per-warp scratch exceeds
+ * GZ_NOALLOC_SCRATCH_BYTES gets GZ_EOVERFLOW, and smaller ones run on as many
+ * warps as the array holds. The graph's views must already exist: call
+ * gz_orient (use_orientation = 1) or one gz_count with this plan first, else
+ * GZ_EINVAL. The first call on each device looks up the array's device address
+ * (once per device, with that device current); make that first call before any
+ * stream capture. Every call shares the array and the call clears its counters
+ * itself; calls whose kernels overlap on the GPU race on it, so the caller must
+ * serialise them. Synchronous on `stream`.
+ */
+gz_status gz_count_noalloc(const gz_plan* p, const gz_graph* g, int use_orientation, void* stream,
+                           uint64_t* out_count);
+
 /*
  * Device scratch gz_count needs for this plan and graph (bytes), so callers can
  * budget memory before admitting a query.

@@ -146,6 +146,27 @@ gz_status prepare_query(const gz_plan* p, const gz_graph* gc, int use_orientatio
     return GZ_OK;
 }
 
+// Like prepare_query for the full root range, but never builds anything: the
+// views the plan needs must already exist (gz_orient, or one gz_count).
+gz_status prepare_check(const gz_plan* p, const gz_graph* g, int use_orientation, Query& q) {
+    if (use_orientation && !g->oriented) {
+        set_error("count: use_orientation = 1 needs gz_orient first");
+        return GZ_EINVAL;
+    }
+    const GzView* v = use_orientation ? &g->ori : &g->orig;
+    if (!v->has_dag || (!p->prog.unit_dag && !v->src)) {
+        set_error("count: the graph's views for this plan are not built yet; run gz_orient or one "
+                  "gz_count with this plan first");
+        return GZ_EINVAL;
+    }
+    q.prog = &p->prog;
+    q.g = g;
+    q.view = v;
+    q.unit_lo = 0;
+    q.unit_hi = p->prog.unit_dag ? v->dag_nnz : g->nnz;
+    return GZ_OK;
+}
+
 LaunchCfg default_cfg() {
     LaunchCfg c;
     c.block_warps = 8;

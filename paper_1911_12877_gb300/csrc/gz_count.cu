@@ -468,7 +468,108 @@ __global__ void __launch_bounds__(256, 2) k_enumerate(const KQ* __restrict__ qs,
     }
 }
 
+// Single-query form of k_enumerate: the descriptor travels as a kernel
+// parameter and all device state (queue counter, count, status, per-warp
+// scratch) lives in one caller-provided region, so launching it needs no
+// device allocation.
+__global__ void __launch_bounds__(256, 2) k_enumerate_one(const __grid_constant__ KQ q,
+                                                       int64_t total_units, int chunk,
+                                                       unsigned long long* __restrict__ work,
+                                                       unsigned long long* __restrict__ count,
+                                                       int* __restrict__ status,
+                                                       int32_t* __restrict__ scratch,
+                                                       int64_t words_per_warp) {
+    extern __shared__ int32_t smem[];
+    const int lane = threadIdx.x & 31;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int32_t* my = scratch + gwarp * words_per_warp;
+    int32_t* sm = smem + (threadIdx.x >> 5) * kWarpSmemWords;
+    WarpState ws;
+    unsigned long long acc = 0;
+    for (;;) {
+        unsigned long long start = 0;
+        if (lane == 0) start = atomicAdd(work, (unsigned long long)chunk);
+        start = __shfl_sync(kFull, start, 0);
+        if ((int64_t)start >= total_units) break;
+        int64_t end = (int64_t)start + chunk;
+        if (end > total_units) end = total_units;
+        for (int64_t u = (int64_t)start; u < end; ++u) process_unit(q, q.unit_lo + u, ws, my, sm, lane, acc, status);
+    }
+    unsigned long long s = warp_sum(acc);
+    if (lane == 0 && s) atomicAdd(count, s);
+}
+
+void fill_kq(const Query& Q, KQ& k, uint64_t* words_out) {
+    memset(&k, 0, sizeof(KQ));
+    k.prog = *Q.prog;
+    const GzView& v = *Q.view;
+    k.rp = v.rp; k.col = v.col; k.drp = v.dag_rp; k.dcol = v.dag_col;
+    if (Q.prog->unit_dag) { k.usrc = v.dag_src; k.ucol = v.dag_col; k.urp = v.dag_rp; }
+    else { k.usrc = v.src; k.ucol = v.col; k.urp = v.rp; }
+    k.unit_lo = Q.unit_lo;
+    k.unit_count = Q.unit_hi - Q.unit_lo;
+    uint64_t off = 0;
+    for (int b = 0; b < Q.prog->nbuf; ++b) {
+        uint64_t cap = (uint64_t)(Q.prog->buf_dag[b] ? v.max_out : Q.g->max_deg);
+        k.buf_off[b] = (int64_t)off;
+        k.buf_cap[b] = (int64_t)cap;
+        off += (cap + 31) & ~31ull;
+    }
+    *words_out = off;
+}
+
 }  // namespace
+
+// Counts one query with every piece of device state inside `region`
+// (kRegionHeader bytes of counters, then scratch_bytes of per-warp scratch);
+// launches fewer warps when the scratch would not hold a full grid. Allocates
+// nothing. Synchronous: the count and status are read back into host locals.
+gz_status count_one_in_region(const Query& Q, const LaunchCfg& cfg, cudaStream_t s, void* region,
+                              uint64_t scratch_bytes, uint64_t* out_count) {
+    KQ k;
+    uint64_t words = 0;
+    fill_kq(Q, k, &words);
+    const int64_t total = Q.unit_hi - Q.unit_lo;
+    *out_count = 0;
+    if (total <= 0) return GZ_OK;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int bw = cfg.block_warps;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate_one, bw * 32, bw * kWarpSmemWords * 4);
+    if (per_sm < 1) per_sm = 1;
+    int64_t warps = (int64_t)sms * per_sm * bw;
+    if (words > 0) {
+        const int64_t fit = (int64_t)(scratch_bytes / (words * sizeof(int32_t)));
+        if (fit < 1) {
+            set_error("count: %llu bytes of scratch per warp exceed the %llu-byte region",
+                      (unsigned long long)(words * 4), (unsigned long long)scratch_bytes);
+            return GZ_EOVERFLOW;
+        }
+        if (fit < warps) warps = fit;
+    }
+    if (warps < bw) bw = (int)warps;
+    const int blocks = (int)(warps / bw);
+    unsigned long long* hdr = reinterpret_cast<unsigned long long*>(region);
+    cudaError_t e = cudaMemsetAsync(region, 0, kRegionHeader, s);
+    if (e == cudaSuccess) {
+        k_enumerate_one<<<blocks, bw * 32, bw * kWarpSmemWords * 4, s>>>(
+            k, total, cfg.chunk > 0 ? cfg.chunk : 1, hdr, hdr + 1, reinterpret_cast<int*>(hdr + 2),
+            reinterpret_cast<int32_t*>(reinterpret_cast<char*>(region) + kRegionHeader), (int64_t)words);
+        GZ_COUNT_LAUNCH();
+        e = cudaGetLastError();
+    }
+    unsigned long long h[3] = {0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, hdr, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "count (region)");
+    if ((int)h[2] != 0) {
+        set_error("count: a scratch buffer overflowed (planner capacity bug)");
+        return GZ_EOVERFLOW;
+    }
+    *out_count = h[1];
+    return GZ_OK;
+}
 
 uint64_t scratch_words_per_warp(const GzProg& p, const gz_graph& g, const GzView& v) {
     uint64_t w = 0;

@@ -122,6 +122,11 @@ gz_status count_launch(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream
                        int* d_status);
 int resident_warps(const LaunchCfg& cfg);
 
+// Bytes of counters (queue, count, status) at the start of a count region.
+constexpr uint64_t kRegionHeader = 256;
+gz_status count_one_in_region(const Query& Q, const LaunchCfg& cfg, cudaStream_t s, void* region,
+                              uint64_t scratch_bytes, uint64_t* out_count);
+
 // clique side (gz_clique.cu): oriented k-cliques as bitsets over the root's out-list
 constexpr int kCliqueMaxOut = 1024;  // largest out-list kept in shared memory
 bool clique_eligible(const GzProg& p, const gz_plan& plan, const GzView& v);
