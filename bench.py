@@ -359,7 +359,195 @@ def run_reference(args, world, rank):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-EXTRA = {}
+# ------------------------------------------------------------------ other workloads
+
+
+def _time_counts(fn, reps, stream, flush=None):
+    """CUDA-event time of fn() per call (ms list), after one untimed call."""
+    import torch
+    out = fn()
+    ms = []
+    for _ in range(reps):
+        if flush is not None:
+            flush_l2(flush)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+        if r != out:
+            raise SystemExit(f"count changed between repetitions: {out} vs {r}")
+    return out, ms
+
+
+def _summary(ms):
+    s = sorted(ms)
+    return {"median_ms": round(statistics.median(s), 4), "min_ms": round(s[0], 4),
+            "p90_ms": round(s[min(len(s) - 1, int(0.9 * len(s)))], 4)}
+
+
+def _line(metric, value, unit, args, world, ms_per_step, config, hib=True, **kw):
+    d = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": hib,
+         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+         "config": config}
+    d.update(kw)
+    return d
+
+
+def run_triangle(args, dist, world, rank, local):
+    """Triangle counting, plain method (restrictions on the original ids, no reindex):
+    ER G(4096, 16/4095), seed 1. L2-resident and launch-latency bound."""
+    import torch
+    import paper_1911_12877_gb300 as gz
+    import synthetic as S
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    g = S.er_triangle()
+    gold = load_golden("er_triangle.json")
+    G = gz.Graph.from_csr(g)
+    p = gz.Plan("triangle")
+    reps = max(20, args.steps)
+    l0 = gz.kernel_launches()
+    c, ms = _time_counts(lambda: gz.count(p, G, orientation=False), reps, stream)
+    launches = gz.kernel_launches() - l0
+    if c != gold["triangle"]["count"]:
+        raise SystemExit(f"triangle count {c} != oracle {gold['triangle']['count']}")
+    e = gold["triangle"]["elems"]
+    med = statistics.median(ms)
+    return _line("intersected elements/s (count time)", e / (med / 1e3), UNIT, args, world, med,
+                 {"workload": "triangle, plain method (original ids), ER n=4096 p=16/4095 seed 1",
+                  "n": g.n, "nnz": g.nnz, "l2": "resident (270 KB CSR); not flushed"},
+                 count=c, elems=e, count_us=round(med * 1e3, 2), timing=_summary(ms),
+                 gpu_launches=launches, note="launch-latency bound: % of HBM is not meaningful")
+
+
+def run_patterns(args, dist, world, rank, local):
+    """Arbitrary patterns with restrictions and generalized orientation on R-MAT
+    (default scale 22, ef 16, seed 22): c4, diamond, paw, house, chordal5."""
+    import torch
+    import paper_1911_12877_gb300 as gz
+    import synthetic as S
+    from synthetic.patterns import PATTERN_SET
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    scale = args.scale or 22
+    g = S.rmat(scale, 16, scale)
+    gold = None
+    if scale == 22 and os.path.exists(os.path.join(GOLDEN, "patterns_rmat22.json")):
+        gold = load_golden("patterns_rmat22.json")
+    G = gz.Graph.from_csr(g)
+    _, t_or = _time_counts(lambda: (G.orient(), 0)[1], 3, stream)
+    names = args.patterns.split(",") if args.patterns else PATTERN_SET
+    res = {}
+    total_ms = 0.0
+    l0 = gz.kernel_launches()
+    for name in names:
+        p = gz.Plan(name)
+        c, ms = _time_counts(lambda: gz.count(p, G, orientation=True), args.steps, stream)
+        r = {"count": c, **_summary(ms)}
+        if gold and name in gold["patterns"]:
+            rec = gold["patterns"][name]
+            for lo, hi, want in rec["samples"]:
+                got = gz.count(p, G, True, lo, hi)
+                if got != want:
+                    raise SystemExit(f"{name} roots [{lo},{hi}): {got} != oracle {want}")
+            r["oracle_samples_ok"] = len(rec["samples"])
+            if "elems" in rec:
+                r["elems"] = rec["elems"]
+                r["elems_per_s"] = rec["elems"] / (r["median_ms"] / 1e3)
+                r["hbm_frac_algorithmic"] = 4 * r["elems_per_s"] / 1e9 / measured_peaks()[0]
+        res[name] = r
+        total_ms += r["median_ms"]
+    launches = gz.kernel_launches() - l0
+    return _line("count time, five patterns (sum of medians)", total_ms, "ms", args, world, total_ms,
+                 {"workload": f"c4, diamond, paw, house, chordal5 with restrictions + orientation, "
+                              f"R-MAT scale {scale} ef 16 seed {scale}", "n": g.n, "nnz": g.nnz,
+                  "l2": "inputs larger than L2"},
+                 hib=False, patterns=res, orient_ms=_summary(t_or), gpu_launches=launches)
+
+
+def run_batched(args, dist, world, rank, local):
+    """64 queries (12 patterns) over 16 R-MAT graphs of scales 10..21 in one
+    gz_count_batch call, against the same 64 run one per gz_count call."""
+    import torch
+    import paper_1911_12877_gb300 as gz
+    import synthetic as S
+    from synthetic.patterns import batch_queries
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    top = args.scale or 21
+    idx = [i for i in range(16) if S.BATCH_SCALES[i] <= top]
+    graphs = {i: gz.Graph.from_csr(S.batch_graph(i)).orient() for i in idx}
+    table = [(gi, name) for gi, name in batch_queries() if gi in graphs]
+    plans = {name: gz.Plan(name) for _, name in table}
+    qp = [plans[n] for _, n in table]
+    qg = [graphs[gi] for gi, _ in table]
+    qo = [True] * len(table)
+    l0 = gz.kernel_launches()
+    batch, ms_b = _time_counts(lambda: gz.count_batch(qp, qg, qo), args.steps, stream)
+    lb = gz.kernel_launches() - l0
+    plain, ms_p = _time_counts(lambda: [gz.count(p, G, True) for p, G in zip(qp, qg)], args.steps,
+                               stream)
+    if batch != plain:
+        raise SystemExit("batched counts differ from one-per-launch counts")
+    mb, mp = statistics.median(ms_b), statistics.median(ms_p)
+    return _line("queries/s, batched (one gz_count_batch call)", len(table) / (mb / 1e3), "queries/s",
+                 args, world, mb,
+                 {"workload": f"{len(table)} queries over {len(graphs)} R-MAT graphs (scales 10..{top}, "
+                              f"ef 8..32, seeds 100+i), query table seed 4", "queries": len(table)},
+                 plain_queries_per_s=len(table) / (mp / 1e3), speedup_vs_plain=mp / mb,
+                 batched=_summary(ms_b), plain=_summary(ms_p), gpu_launches_per_batch=lb // (args.steps + 1),
+                 counts=[int(x) for x in batch])
+
+
+def run_served(args, dist, world, rank, local):
+    """Poisson request stream over a device-resident R-MAT graph (default scale 24):
+    continuous batching vs FIFO one query per launch, p50/p99 latency."""
+    import numpy as np
+    import torch
+    import paper_1911_12877_gb300 as gz
+    import synthetic as S
+    from synthetic.patterns import SERVED_PATTERNS
+    torch.cuda.set_device(local)
+    scale = args.scale or 24
+    g = S.rmat(scale, 16, scale)
+    G = gz.Graph.from_csr(g).orient()
+    plans = [gz.Plan(n) for n in SERVED_PATTERNS]
+    alone = [gz.count(p, G, True) for p in plans]
+    nreq = args.requests
+    out = {}
+    for lam in [float(x) for x in args.rates.split(",")]:
+        rng = np.random.default_rng(5)
+        arr = np.cumsum(rng.exponential(1e9 / lam, nreq)).astype(np.int64)
+        pidx = rng.integers(0, len(plans), nreq).astype(np.int32)
+        gidx = np.zeros(nreq, np.int32)
+        rec = {}
+        for mode in ("served", "fifo"):
+            srv = gz.Server(max_inflight=4, max_batch=64)
+            counts, lat, st = srv.replay(plans, [G], [1] * nreq, arr, pidx, gidx, fifo=(mode == "fifo"))
+            srv.close()
+            if [int(c) for c in counts] != [alone[i] for i in pidx]:
+                raise SystemExit(f"{mode} counts differ from counts alone")
+            ms = np.sort(lat) / 1e6
+            rec[mode] = {"p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+                         "achieved_rps": st["achieved_rps"], "max_queue": int(st["max_queue"]),
+                         "launches": int(st["launches"]), "wall_s": st["wall_s"]}
+        out[str(lam)] = rec
+    lam0 = str(float(args.rates.split(",")[-1]))
+    s = out[lam0]["served"]
+    return _line("p99 latency, served (continuous batching)", s["p99_ms"], "ms", args, world,
+                 1e3 * s["wall_s"] / nreq,
+                 {"workload": f"Poisson stream of {nreq} requests over {SERVED_PATTERNS}, R-MAT scale "
+                              f"{scale} ef 16 seed {scale} (+ oriented copy) resident",
+                  "rates_per_s": args.rates},
+                 hib=False, rates=out, counts_alone=dict(zip(SERVED_PATTERNS, alone)))
+
+
+EXTRA = {"triangle": run_triangle, "patterns": run_patterns, "batched": run_batched,
+         "served": run_served}
 
 
 def main(argv=None):
@@ -372,6 +560,10 @@ def main(argv=None):
                     choices=["clique", "triangle", "patterns", "batched", "served"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scale", type=int, default=0, help="R-MAT scale override (smaller cases)")
+    ap.add_argument("--patterns", default="", help="patterns config: comma-separated subset")
+    ap.add_argument("--requests", type=int, default=2000, help="served config: requests per rate")
+    ap.add_argument("--rates", default="12.5,25,50,100,200", help="served config: Poisson rates")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "gz":
         args.warmup = 3

@@ -72,3 +72,35 @@ def adjacency(name_or_edges, k: int | None = None) -> np.ndarray:
     for i, j in edges:
         a[i, j] = a[j, i] = 1
     return a
+
+
+def batch_queries(n_graphs: int = 16, per_graph: int = 4, seed: int = 4, small_scales=None):
+    """Query table of the batched workload: (graph index, pattern name) pairs.
+
+    ``per_graph`` queries per graph (64 in all), every pattern of BATCH_PATTERNS at
+    least four times, and the difference-heavy sparse patterns only on the graphs
+    listed in ``small_scales`` (indices of graphs of R-MAT scale <= 14), because
+    their induced enumeration on hub vertices costs about the sum of cubed degrees.
+    Seeded; the table is an input, not a result.
+    """
+    rng = np.random.default_rng(seed)
+    small = sorted(small_scales) if small_scales is not None else [0, 1, 2, 3, 4, 12, 13]
+    slots = [(g, j) for g in range(n_graphs) for j in range(per_graph)]
+    small_slots = [s for s in slots if s[0] in small]
+    big_slots = [s for s in slots if s[0] not in small]
+    table = {}
+    sparse = [p for p in BATCH_PATTERNS if p in BATCH_SPARSE]
+    dense = [p for p in BATCH_PATTERNS if p not in BATCH_SPARSE]
+    order = rng.permutation(len(small_slots))
+    need = [p for p in sparse for _ in range(4)]
+    for p, i in zip(need, order):
+        table[small_slots[i]] = p
+    free = [small_slots[i] for i in order[len(need):]] + big_slots
+    free = [free[i] for i in rng.permutation(len(free))]
+    need = [p for p in dense for _ in range(4)]
+    for p, s in zip(need, free):
+        table[s] = p
+    for s in free[len(need):]:
+        pool = BATCH_PATTERNS if s[0] in small else dense
+        table[s] = pool[int(rng.integers(len(pool)))]
+    return [(g, table[(g, j)]) for g, j in slots]

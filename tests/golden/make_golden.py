@@ -64,7 +64,12 @@ def clique():
     _dump("clique_rmat20.json", rec)
 
 
-PATTERN_SAMPLES = [(20000, 20004), (300000, 300400), (2000000, 2010000)]
+# Root ranges (reindexed ids) of the arbitrary-pattern workload: a top hub block, two
+# mid-degree blocks and a low-degree block. Each range is grown from width 1 by
+# doubling while the oracle stays within a few seconds on it, so the sample costs
+# the same order of CPU time whatever the pattern.
+PATTERN_STARTS = [64, 20000, 300000, 1000000]
+PATTERN_MAX_W = 4096
 
 
 def patterns():
@@ -73,10 +78,21 @@ def patterns():
     rec = {"graph": g.name, "n": g.n, "nnz": g.nnz, "oriented": True, "patterns": {}}
     for name in PATTERN_SET:
         a, order = _plan(name)
-        t = time.time()
-        samples = [[lo, hi, O.count_nested(a, order, go, lo, hi)[0]] for lo, hi in PATTERN_SAMPLES]
+        t0 = time.time()
+        samples = []
+        for s in PATTERN_STARTS:
+            w, last = 1, None
+            while True:
+                t = time.time()
+                c = O.count_nested(a, order, go, s, s + w)[0]
+                dt = time.time() - t
+                last = [s, s + w, c]
+                if dt > 4.0 or w >= PATTERN_MAX_W:
+                    break
+                w *= 2
+            samples.append(last)
         rec["patterns"][name] = {"order": order, "samples": samples,
-                                 "oracle_s": round(time.time() - t, 1)}
+                                 "oracle_s": round(time.time() - t0, 1)}
         print(name, rec["patterns"][name], flush=True)
     _dump("patterns_rmat22.json", rec)
 
