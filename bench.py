@@ -426,7 +426,13 @@ def run_triangle(args, dist, world, rank, local):
 
 def run_patterns(args, dist, world, rank, local):
     """Arbitrary patterns with restrictions and generalized orientation on R-MAT
-    (default scale 22, ef 16, seed 22): c4, diamond, paw, house, chordal5."""
+    (default scale 22, ef 16, seed 22): c4, diamond, paw, house, chordal5.
+
+    Per pattern: the oracle's sampled root ranges (hub blocks to low-degree
+    blocks) are counted and timed, each count checked against the stored oracle
+    value, and E over those ranges / their count time gives the throughput. The
+    full count is timed for the patterns in --full (its cost on this graph is
+    listed in the design notes for the others)."""
     import torch
     import paper_1911_12877_gb300 as gz
     import synthetic as S
@@ -441,32 +447,43 @@ def run_patterns(args, dist, world, rank, local):
     G = gz.Graph.from_csr(g)
     _, t_or = _time_counts(lambda: (G.orient(), 0)[1], 3, stream)
     names = args.patterns.split(",") if args.patterns else PATTERN_SET
+    if args.full:
+        full = set(args.full.split(","))
+    else:
+        full = {"c4", "diamond"} if scale == 22 else set(names)
+    peak = measured_peaks()[0]
     res = {}
-    total_ms = 0.0
+    tot_e, tot_ms = 0, 0.0
     l0 = gz.kernel_launches()
     for name in names:
         p = gz.Plan(name)
-        c, ms = _time_counts(lambda: gz.count(p, G, orientation=True), args.steps, stream)
-        r = {"count": c, **_summary(ms)}
+        r = {}
         if gold and name in gold["patterns"]:
-            rec = gold["patterns"][name]
-            for lo, hi, want in rec["samples"]:
-                got = gz.count(p, G, True, lo, hi)
+            e_s, ms_s = 0, 0.0
+            for lo, hi, want, e in gold["patterns"][name]["samples"]:
+                got, ms = _time_counts(lambda: gz.count(p, G, True, lo, hi), args.steps, stream)
                 if got != want:
                     raise SystemExit(f"{name} roots [{lo},{hi}): {got} != oracle {want}")
-            r["oracle_samples_ok"] = len(rec["samples"])
-            if "elems" in rec:
-                r["elems"] = rec["elems"]
-                r["elems_per_s"] = rec["elems"] / (r["median_ms"] / 1e3)
-                r["hbm_frac_algorithmic"] = 4 * r["elems_per_s"] / 1e9 / measured_peaks()[0]
+                e_s += e
+                ms_s += statistics.median(ms)
+            r["sampled"] = {"ranges": len(gold["patterns"][name]["samples"]), "elems": e_s,
+                            "ms": round(ms_s, 3), "elems_per_s": e_s / (ms_s / 1e3),
+                            "hbm_frac_algorithmic": round(4 * e_s / (ms_s / 1e3) / 1e9 / peak, 4),
+                            "oracle_parity": "ok"}
+            tot_e += e_s
+            tot_ms += ms_s
+        if name in full:
+            c, ms = _time_counts(lambda: gz.count(p, G, orientation=True), args.steps, stream)
+            r["full"] = {"count": c, **_summary(ms)}
         res[name] = r
-        total_ms += r["median_ms"]
     launches = gz.kernel_launches() - l0
-    return _line("count time, five patterns (sum of medians)", total_ms, "ms", args, world, total_ms,
+    value = tot_e / (tot_ms / 1e3) if tot_ms > 0 else None
+    return _line("intersected elements/s over the oracle's sampled root ranges", value, UNIT, args,
+                 world, tot_ms,
                  {"workload": f"c4, diamond, paw, house, chordal5 with restrictions + orientation, "
                               f"R-MAT scale {scale} ef 16 seed {scale}", "n": g.n, "nnz": g.nnz,
-                  "l2": "inputs larger than L2"},
-                 hib=False, patterns=res, orient_ms=_summary(t_or), gpu_launches=launches)
+                  "l2": "graph larger than L2; not flushed between ranges"},
+                 patterns=res, orient_ms=_summary(t_or), gpu_launches=launches)
 
 
 def run_batched(args, dist, world, rank, local):
@@ -562,6 +579,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scale", type=int, default=0, help="R-MAT scale override (smaller cases)")
     ap.add_argument("--patterns", default="", help="patterns config: comma-separated subset")
+    ap.add_argument("--full", default="", help="patterns config: patterns whose full count is timed "
+                    "(default c4,diamond at scale 22, all below)")
     ap.add_argument("--requests", type=int, default=2000, help="served config: requests per rate")
     ap.add_argument("--rates", default="12.5,25,50,100,200", help="served config: Poisson rates")
     args = ap.parse_args(argv)

@@ -122,10 +122,13 @@ gz_status prepare_query(const gz_plan* p, const gz_graph* gc, int use_orientatio
         if (st != GZ_OK) return st;
     }
     q.prog = &p->prog;
+    q.plan = p;
     q.g = g;
     q.view = v;
     if (root_lo < 0) root_lo = 0;
     if (root_hi < 0 || root_hi > g->n) root_hi = g->n;
+    q.root_lo = root_lo;
+    q.root_hi = root_hi;
     if (root_lo >= root_hi) {
         q.unit_lo = q.unit_hi = 0;
         return GZ_OK;
@@ -174,27 +177,60 @@ LaunchCfg default_cfg() {
     return c;
 }
 
-// Runs nq queries in one launch and copies their counts to the host.
+uint64_t mixed_scratch_bytes(const Query* qs, int nq, const LaunchCfg& cfg) {
+    uint64_t words = 0;
+    for (int i = 0; i < nq; ++i) {
+        const Query& q = qs[i];
+        if (q.plan && clique_eligible(*q.prog, *q.plan, *q.view) && q.view->max_out <= kCliqueMaxOut)
+            continue;
+        words = std::max(words, scratch_words_per_warp(*q.prog, *q.g, *q.view));
+    }
+    return (uint64_t)resident_warps(cfg) * words * sizeof(int32_t);
+}
+
+gz_status launch_mixed(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream_t s,
+                       unsigned long long* d_counts, int* d_status, unsigned long long* d_work,
+                       void* scratch, uint64_t scratch_bytes) {
+    std::vector<Query> gen;
+    for (int i = 0; i < nq; ++i) {
+        Query q = qs[i];
+        q.out_slot = i;
+        if (q.unit_hi <= q.unit_lo) continue;
+        if (q.plan && clique_eligible(*q.prog, *q.plan, *q.view)) {
+            const int64_t lo = q.root_lo < 0 ? 0 : q.root_lo;
+            const int64_t hi = (q.root_hi < 0 || q.root_hi > q.g->n) ? q.g->n : q.root_hi;
+            gz_status st = clique_launch(q.plan->k, *q.view, q.g->n, lo, hi, s, d_counts + i,
+                                         d_work + 2 * i);
+            if (st != GZ_OK) return st;
+            if (q.view->max_out <= kCliqueMaxOut) continue;
+            q.min_root_out = kCliqueMaxOut + 1;  // roots the bitset kernels leave out
+        }
+        gen.push_back(q);
+    }
+    if (gen.empty()) return GZ_OK;
+    return count_launch(gen.data(), (int)gen.size(), cfg, s, d_counts, scratch, scratch_bytes, d_status);
+}
+
+// Runs nq queries (one launch_mixed) and copies their counts to the host.
 gz_status run_queries(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream_t s,
                       uint64_t* out_counts) {
-    uint64_t words = 0;
-    for (int i = 0; i < nq; ++i)
-        words = std::max(words, scratch_words_per_warp(*qs[i].prog, *qs[i].g, *qs[i].view));
-    const uint64_t need = (uint64_t)resident_warps(cfg) * words * sizeof(int32_t);
+    const uint64_t need = mixed_scratch_bytes(qs, nq, cfg);
     Arena& a = arena();
     std::lock_guard<std::mutex> lk(a.mu);
     gz_status st = arena_reserve(a, need);
     if (st != GZ_OK) return st;
+    // counts [nq], status, clique work counters [2 nq]
+    const size_t words = (size_t)nq + 1 + 2 * (size_t)nq;
     unsigned long long* d = nullptr;
-    cudaError_t e = cudaMallocAsync(&d, sizeof(unsigned long long) * (nq + 1), s);
+    cudaError_t e = cudaMallocAsync(&d, sizeof(unsigned long long) * words, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync counts");
     int* d_status = reinterpret_cast<int*>(d + nq);
-    e = cudaMemsetAsync(d, 0, sizeof(unsigned long long) * (nq + 1), s);
+    e = cudaMemsetAsync(d, 0, sizeof(unsigned long long) * words, s);
     if (e != cudaSuccess) {
         cudaFreeAsync(d, s);
         return cuda_fail(e, "memset counts");
     }
-    st = count_launch(qs, nq, cfg, s, d, a.ptr, a.bytes, d_status);
+    st = launch_mixed(qs, nq, cfg, s, d, d_status, d + nq + 1, a.ptr, a.bytes);
     std::vector<unsigned long long> h(nq + 1);
     if (st == GZ_OK) {
         e = cudaMemcpyAsync(h.data(), d, sizeof(unsigned long long) * (nq + 1), cudaMemcpyDeviceToHost, s);
@@ -209,24 +245,6 @@ gz_status run_queries(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream_
     }
     for (int i = 0; i < nq; ++i) out_counts[i] = h[i];
     return GZ_OK;
-}
-
-// Oriented k-clique counting through the bitset kernels (gz_clique.cu).
-gz_status run_clique(int k, const GzView& v, int64_t lo, int64_t hi, cudaStream_t s, uint64_t* out) {
-    unsigned long long* d = nullptr;
-    cudaError_t e = cudaMallocAsync(&d, sizeof(unsigned long long) * 3, s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync clique");
-    e = cudaMemsetAsync(d, 0, sizeof(unsigned long long) * 3, s);
-    gz_status st = e == cudaSuccess ? clique_launch(k, v, lo, hi, s, d, d + 1) : cuda_fail(e, "memset");
-    unsigned long long h = 0;
-    if (st == GZ_OK) {
-        e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) st = cuda_fail(e, "clique count");
-    }
-    cudaFreeAsync(d, s);
-    if (st == GZ_OK) *out = h;
-    return st;
 }
 
 bool check_graph(const gz_graph* g, const char* who) {
@@ -481,11 +499,6 @@ gz_status gz_count_ex(const gz_plan* p, const gz_graph* g, const gz_count_opts* 
     if (o.chunk > 0) cfg.chunk = o.chunk;
     *out_count = 0;
     if (q.unit_hi <= q.unit_lo) return GZ_OK;
-    if (clique_eligible(p->prog, *p, *q.view)) {
-        int64_t lo = o.root_lo < 0 ? 0 : o.root_lo;
-        int64_t hi = (o.root_hi < 0 || o.root_hi > g->n) ? g->n : o.root_hi;
-        return run_clique(p->k, *q.view, lo, hi, s, out_count);
-    }
     return run_queries(&q, 1, cfg, s, out_count);
 }
 

@@ -16,7 +16,10 @@
 //    cooperatively (each row streams the shorter of O[0, a) and N(O[a])),
 //    then the (a, b) pairs of the local DAG are spread over all threads.
 #include <algorithm>
+#include <climits>
+#include <cmath>
 #include <cstdio>
+#include <vector>
 
 #include "gz_internal.h"
 
@@ -26,6 +29,9 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kThreads = 256;
+constexpr int kBigPop = 16;     // roots per queue slot of the big kernel; most are skipped
+constexpr int kHeavyD = 128;    // out-degree from which a root is split over several CTAs
+constexpr uint64_t kHeavyRowWords = 1ull << 29;  // budget for prebuilt heavy rows (2 GiB)
 
 __device__ __forceinline__ bool has(const int32_t* __restrict__ R, int n, int32_t x) {
     int lo = 0, len = n;
@@ -142,63 +148,138 @@ __global__ void __launch_bounds__(kThreads) k_clique_small(const int64_t* __rest
     if (threadIdx.x == 0 && s) atomicAdd(count, s);
 }
 
-// Roots with 32 < |O| <= max_out: one CTA per root. Shared memory layout:
-// rows [max_out * W] words, O [max_out], pre [max_out + 1].
+// Builds row(a), a in [1, d), of the root whose out-list O[0, d) is in shared
+// memory into rows (stride Ws, zeroed): one warp per a streams the shorter of
+// O[0, a) and N'(O[a]) and looks each element up in the other (a binary search
+// in shared memory, or in the global out-list), so a root costs about
+// sum_a min(a, |N'(O[a])|) lookups.
+__device__ __forceinline__ void build_rows(const int64_t* __restrict__ drp,
+                                           const int32_t* __restrict__ dcol, const int32_t* O,
+                                           int d, uint32_t* rows, int Ws, int lane, int warp,
+                                           int nwarps) {
+    for (int a = warp + 1; a < d; a += nwarps) {
+        const int32_t u = O[a];
+        const int64_t ub = drp[u];
+        const int du = (int)(drp[u + 1] - ub);
+        uint32_t* ra = rows + (size_t)a * Ws;
+        if (du < a) {
+            for (int i = lane; i < du; i += 32) {
+                const int b = index_of(O, a, __ldg(dcol + ub + i));
+                if (b >= 0) atomicOr(ra + (b >> 5), 1u << (b & 31));
+            }
+        } else {
+            for (int b0 = 0; b0 < a; b0 += 32) {
+                const int b = b0 + lane;
+                const bool in = b < a && has(dcol + ub, du, O[b]);
+                const uint32_t m = __ballot_sync(kFull, in);
+                if (lane == 0) ra[b0 >> 5] = m;
+            }
+        }
+    }
+}
+
+// Rows of every heavy root, built once into global memory (one CTA per root,
+// grid-stride), so the parts of a heavy root copy them instead of rebuilding.
+// hr[i] = (root, unused, word offset of its rows in grows). Shared memory as in
+// k_clique_big (rows, O).
+__global__ void __launch_bounds__(kThreads) k_clique_rows(const int64_t* __restrict__ drp,
+                                                          const int32_t* __restrict__ dcol,
+                                                          const int4* __restrict__ hr, int nh,
+                                                          int max_out,
+                                                          uint32_t* __restrict__ grows) {
+    extern __shared__ uint32_t sm[];
+    const int Wsmax = ((max_out + 31) >> 5) | 1;
+    uint32_t* rows = sm;
+    int32_t* O = reinterpret_cast<int32_t*>(sm + (size_t)max_out * Wsmax);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int h = blockIdx.x; h < nh; h += gridDim.x) {
+        const int64_t v = hr[h].x;
+        const int64_t ob = drp[v];
+        const int d = (int)(drp[v + 1] - ob);
+        const int Ws = ((d + 31) >> 5) | 1;
+        for (int i = threadIdx.x; i < d; i += kThreads) O[i] = dcol[ob + i];
+        for (int i = threadIdx.x; i < d * Ws; i += kThreads) rows[i] = 0;
+        __syncthreads();
+        build_rows(drp, dcol, O, d, rows, Ws, lane, warp, kThreads / 32);
+        __syncthreads();
+        uint32_t* dst = grows + (uint32_t)hr[h].z;
+        for (int i = threadIdx.x; i < d * Ws; i += kThreads) dst[i] = rows[i];
+        __syncthreads();
+    }
+}
+
+// Roots with 32 < |O| <= max_out: one CTA per root, or per part of a heavy
+// root. Shared memory: rows [max_out * Wsmax] words (row stride Ws = W | 1 for
+// the current root, odd so that threads reading word w of different rows hit
+// different banks), O [max_out], pre [max_out + 1].
+//
+// Rows come from build_rows or, for a part of a heavy root, are copied from the
+// rows k_clique_rows built once for that root. pre[a] counts the local DAG
+// edges (a, b), b < a, before row a; edge p is then one work item: a thread
+// finds its (a, b) and runs the remaining K - 3 loops over row(a) & row(b).
+// Consecutive threads take consecutive edges (same a, neighbouring b), so row(a)
+// reads are broadcasts and row(b) reads fall in distinct banks. A heavy root's
+// parts take interleaved blocks of kThreads edges.
 template <int K>
 __global__ void __launch_bounds__(kThreads) k_clique_big(const int64_t* __restrict__ drp,
                                                          const int32_t* __restrict__ dcol,
                                                          int64_t root_lo, int64_t root_hi,
-                                                         int max_out,
+                                                         int max_out, int heavy_d,
+                                                         const int4* __restrict__ heavy,
+                                                         int nheavy,
+                                                         const uint32_t* __restrict__ grows,
                                                          unsigned long long* __restrict__ work,
                                                          unsigned long long* __restrict__ count) {
     extern __shared__ uint32_t sm[];
     __shared__ unsigned long long red[kThreads / 32];
     __shared__ int64_t s_root;
-    const int Wmax = (max_out + 31) >> 5;
+    const int Wsmax = ((max_out + 31) >> 5) | 1;
     uint32_t* rows = sm;
-    int32_t* O = reinterpret_cast<int32_t*>(sm + (size_t)max_out * Wmax);
+    int32_t* O = reinterpret_cast<int32_t*>(sm + (size_t)max_out * Wsmax);
     int32_t* pre = O + max_out;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = kThreads / 32;
     unsigned long long acc = 0;
-    constexpr int kPop = 16;  // roots per queue pop; most of them are small and skipped
+    const int64_t nchunks = (root_hi - root_lo + kBigPop - 1) / kBigPop;
     for (;;) {
-        if (threadIdx.x == 0) s_root = root_lo + (int64_t)atomicAdd(work, (unsigned long long)kPop);
+        // queue slots: [0, nheavy) one part of a heavy root each (heaviest first),
+        // then chunks of kBigPop consecutive roots (heavy ones skipped there)
+        if (threadIdx.x == 0) s_root = (int64_t)atomicAdd(work, 1ull);
         __syncthreads();
-        const int64_t v0 = s_root;
+        const int64_t slot = s_root;
         __syncthreads();
-        if (v0 >= root_hi) break;
-      for (int r = 0; r < kPop; ++r) {
+        if (slot >= nheavy + nchunks) break;
+        int64_t v0, nr;
+        int part = 0, parts = 1;
+        const uint32_t* src = nullptr;  // prebuilt rows of a heavy root
+        if (slot < nheavy) {
+            const int4 h = heavy[slot];
+            v0 = h.x;
+            nr = 1;
+            part = h.y & 0xffff;
+            parts = h.y >> 16;
+            src = grows + (uint32_t)h.z;
+        } else {
+            v0 = root_lo + (slot - nheavy) * kBigPop;
+            nr = kBigPop;
+        }
+      for (int r = 0; r < nr; ++r) {
         const int64_t v = v0 + r;
         if (v >= root_hi) break;
         const int64_t ob = drp[v];
         const int d = (int)(drp[v + 1] - ob);
-        if (d <= 32 || d > max_out) continue;
-        const int W = (d + 31) >> 5;
+        if (d <= 32 || d > max_out || (slot >= nheavy && d >= heavy_d)) continue;
+        const int Ws = ((d + 31) >> 5) | 1;
         for (int i = threadIdx.x; i < d; i += kThreads) O[i] = dcol[ob + i];
-        for (int i = threadIdx.x; i < d * W; i += kThreads) rows[i] = 0;
-        __syncthreads();
-        // rows: warp per a; stream the shorter of O[0, a) and N(O[a])
-        for (int a = warp + 1; a < d; a += nwarps) {
-            const int32_t u = O[a];
-            const int64_t ub = drp[u];
-            const int du = (int)(drp[u + 1] - ub);
-            uint32_t* ra = rows + (size_t)a * W;
-            if (du < a) {
-                for (int i = lane; i < du; i += 32) {
-                    const int b = index_of(O, a, __ldg(dcol + ub + i));
-                    if (b >= 0) atomicOr(ra + (b >> 5), 1u << (b & 31));
-                }
-            } else {
-                for (int b0 = 0; b0 < a; b0 += 32) {
-                    const int b = b0 + lane;
-                    const bool in = b < a && has(dcol + ub, du, O[b]);
-                    const uint32_t m = __ballot_sync(kFull, in);
-                    if (lane == 0) ra[b0 >> 5] = m;
-                }
-            }
+        if (src) {
+            for (int i = threadIdx.x; i < d * Ws; i += kThreads) rows[i] = __ldg(src + i);
+            __syncthreads();
+        } else {
+            for (int i = threadIdx.x; i < d * Ws; i += kThreads) rows[i] = 0;
+            __syncthreads();
+            build_rows(drp, dcol, O, d, rows, Ws, lane, warp, nwarps);
+            __syncthreads();
         }
-        __syncthreads();
         // pre[a] = number of local edges (a, b), b < a, before row a
         if (warp == 0) {
             int run = 0;
@@ -206,10 +287,10 @@ __global__ void __launch_bounds__(kThreads) k_clique_big(const int64_t* __restri
                 const int a = a0 + lane;
                 int c = 0;
                 if (a < d)
-                    for (int w = 0; w < W; ++w) c += __popc(rows[(size_t)a * W + w]);
+                    for (int w = 0, wa = (a + 31) >> 5; w < wa; ++w) c += __popc(rows[(size_t)a * Ws + w]);
                 int incl = c;
                 for (int o = 1; o < 32; o <<= 1) {
-                    int t = __shfl_up_sync(kFull, incl, o);
+                    const int t = __shfl_up_sync(kFull, incl, o);
                     if (lane >= o) incl += t;
                 }
                 if (a < d) pre[a] = run + incl - c;
@@ -219,7 +300,9 @@ __global__ void __launch_bounds__(kThreads) k_clique_big(const int64_t* __restri
         }
         __syncthreads();
         const int pairs = pre[d];
-        for (int p = threadIdx.x; p < pairs; p += kThreads) {
+        for (int blk = part; blk * kThreads < pairs; blk += parts) {
+            const int p = blk * kThreads + threadIdx.x;
+            if (p >= pairs) continue;
             int lo = 0, hi = d - 1;  // last a with pre[a] <= p
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
@@ -227,9 +310,9 @@ __global__ void __launch_bounds__(kThreads) k_clique_big(const int64_t* __restri
             }
             const int a = lo;
             int j = p - pre[a];
-            const uint32_t* ra = rows + (size_t)a * W;
+            const uint32_t* ra = rows + (size_t)a * Ws;
             int b = -1;
-            for (int w = 0; w < W; ++w) {
+            for (int w = 0; w < Ws; ++w) {
                 uint32_t m = ra[w];
                 const int c = __popc(m);
                 if (j < c) {
@@ -239,7 +322,7 @@ __global__ void __launch_bounds__(kThreads) k_clique_big(const int64_t* __restri
                 }
                 j -= c;
             }
-            acc += count_pair<K>(rows, W, a, b);
+            acc += count_pair<K>(rows, Ws, a, b);
         }
         __syncthreads();
       }
@@ -248,9 +331,76 @@ __global__ void __launch_bounds__(kThreads) k_clique_big(const int64_t* __restri
     if (threadIdx.x == 0 && s) atomicAdd(count, s);
 }
 
+// Roots with out-degree >= kHeavyD (one pass to count, one to fill).
+__global__ void k_collect_heavy(const int64_t* __restrict__ drp, int64_t n, int heavy_d,
+                                int2* __restrict__ out, unsigned long long* __restrict__ cnt,
+                                int64_t cap) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int64_t d = drp[v + 1] - drp[v];
+        if (d >= heavy_d) {
+            const unsigned long long i = atomicAdd(cnt, 1ull);
+            if (out && (int64_t)i < cap) out[i] = make_int2((int)v, (int)d);
+        }
+    }
+}
+
+// Fills v.heavy (sorted by root id) once per out-list build.
+gz_status gather_heavy(GzView& v, int64_t n, cudaStream_t s) {
+    if (v.heavy_built) return GZ_OK;
+    v.heavy.clear();
+    if (n <= 0 || v.max_out < kHeavyD) {
+        v.heavy_built = true;
+        return GZ_OK;
+    }
+    unsigned long long* cnt = nullptr;
+    cudaError_t e = cudaMallocAsync(&cnt, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "clique: heavy roots");
+    int64_t gb = (n + 255) / 256;
+    const int grid = (int)std::min<int64_t>(gb, 152 * 16);
+    unsigned long long h = 0;
+    e = cudaMemsetAsync(cnt, 0, sizeof(h), s);
+    if (e == cudaSuccess) {
+        k_collect_heavy<<<grid, 256, 0, s>>>(v.dag_rp, n, kHeavyD, nullptr, cnt, 0);
+        GZ_COUNT_LAUNCH();
+        e = cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int2* d_out = nullptr;
+    std::vector<int2> tmp(h);
+    if (e == cudaSuccess && h > 0) {
+        e = cudaMallocAsync(&d_out, sizeof(int2) * h, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s);
+        if (e == cudaSuccess) {
+            k_collect_heavy<<<grid, 256, 0, s>>>(v.dag_rp, n, kHeavyD, d_out, cnt, (int64_t)h);
+            GZ_COUNT_LAUNCH();
+            e = cudaMemcpyAsync(tmp.data(), d_out, sizeof(int2) * h, cudaMemcpyDeviceToHost, s);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFreeAsync(d_out, s);
+    }
+    cudaFreeAsync(cnt, s);
+    if (e != cudaSuccess) return cuda_fail(e, "clique: heavy roots");
+    v.heavy.reserve(h);
+    for (const int2& x : tmp) v.heavy.emplace_back(x.x, x.y);
+    std::sort(v.heavy.begin(), v.heavy.end());
+    v.heavy_built = true;
+    return GZ_OK;
+}
+
+// Parts a heavy root is split into: about its work (d^2 for K = 4, d^3 beyond)
+// over that of a root of out-degree kHeavyD, at most 64 and at most d. Parts
+// copy the root's prebuilt rows, so a part costs little beyond its share.
+int parts_for(int K, int d) {
+    const double r = (double)d / kHeavyD;
+    const double w = K == 4 ? r * r : r * r * r;
+    const int p = (int)std::ceil(w);
+    return std::max(1, std::min(std::min(p, 64), d));
+}
+
 template <int K>
-gz_status launch_k(const GzView& v, int64_t lo, int64_t hi, cudaStream_t s, unsigned long long* d_count,
-                   unsigned long long* d_work) {
+gz_status launch_k(const GzView& v, int64_t n, int64_t lo, int64_t hi, cudaStream_t s,
+                   unsigned long long* d_count, unsigned long long* d_work) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -261,17 +411,84 @@ gz_status launch_k(const GzView& v, int64_t lo, int64_t hi, cudaStream_t s, unsi
     if (need_small < blocks) blocks = (int)std::max<int64_t>(1, need_small);
     k_clique_small<K><<<blocks, kThreads, 0, s>>>(v.dag_rp, v.dag_col, lo, hi, d_work, d_count);
     GZ_COUNT_LAUNCH();
-    if (v.max_out > 32) {
-        const int mo = (int)v.max_out;
-        const size_t smem = ((size_t)mo * ((mo + 31) / 32) + 2 * (size_t)mo + 2) * 4;
+    if (v.max_out <= 32) {
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? GZ_OK : cuda_fail(e, "clique launch");
+    }
+    const int mo = (int)std::min<int64_t>(v.max_out, kCliqueMaxOut);
+    GzView& mv = const_cast<GzView&>(v);
+    gz_status st = gather_heavy(mv, n, s);
+    if (st != GZ_OK) return st;
+    // heavy roots of [lo, hi) that fit the kernel, heaviest first, with the word
+    // offset of their prebuilt rows (16-byte aligned) and their parts
+    std::vector<std::pair<int32_t, int32_t>> hr;
+    auto it = std::lower_bound(mv.heavy.begin(), mv.heavy.end(), std::make_pair((int32_t)lo, INT32_MIN));
+    for (; it != mv.heavy.end() && it->first < hi; ++it)
+        if (it->second <= mo) hr.push_back(*it);
+    std::stable_sort(hr.begin(), hr.end(), [](const std::pair<int32_t, int32_t>& a,
+                                              const std::pair<int32_t, int32_t>& b) {
+        return a.second > b.second;
+    });
+    std::vector<int4> roots_rows;
+    std::vector<int4> ent;
+    uint64_t words = 0;
+    for (const auto& x : hr) {
+        const uint64_t sz = (uint64_t)x.second * (((x.second + 31) / 32) | 1);
+        if (words + sz > kHeavyRowWords) break;  // the rest run unsplit, rows built in place
+        roots_rows.push_back(make_int4(x.first, 0, (int)words, 0));
+        const int parts = parts_for(K, x.second);
+        for (int p = 0; p < parts; ++p) ent.push_back(make_int4(x.first, p | (parts << 16), (int)words, 0));
+        words += (sz + 3) & ~3ull;
+    }
+    // heavy roots beyond the row budget are not in the list: the chunk slots
+    // must not skip them, so the split threshold becomes their out-degree + 1
+    int heavy_d = kHeavyD;
+    if (roots_rows.size() < hr.size()) heavy_d = mo + 1;
+    if (heavy_d > mo) {
+        roots_rows.clear();
+        ent.clear();
+        words = 0;
+    }
+    const size_t smem = ((size_t)mo * (((mo + 31) / 32) | 1) + 2 * (size_t)mo + 1) * 4;
+    const size_t smem_rows = ((size_t)mo * (((mo + 31) / 32) | 1) + mo) * 4;
+    int4* d_ent = nullptr;
+    int4* d_hr = nullptr;
+    uint32_t* grows = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!ent.empty()) {
+        e = cudaMallocAsync(&d_ent, sizeof(int4) * (ent.size() + roots_rows.size()), s);
+        if (e == cudaSuccess) e = cudaMallocAsync(&grows, sizeof(uint32_t) * words, s);
+        if (e != cudaSuccess) {
+            if (d_ent) cudaFreeAsync(d_ent, s);
+            return cuda_fail(e, "clique: heavy rows");
+        }
+        d_hr = d_ent + ent.size();
+        e = cudaMemcpyAsync(d_ent, ent.data(), sizeof(int4) * ent.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_hr, roots_rows.data(), sizeof(int4) * roots_rows.size(),
+                                cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) {
+            cudaFuncSetAttribute(k_clique_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows);
+            int rb = sms * 2;
+            if ((int64_t)roots_rows.size() < rb) rb = (int)roots_rows.size();
+            k_clique_rows<<<rb, kThreads, smem_rows, s>>>(v.dag_rp, v.dag_col, d_hr,
+                                                         (int)roots_rows.size(), mo, grows);
+            GZ_COUNT_LAUNCH();
+        }
+    }
+    if (e == cudaSuccess) {
         cudaFuncSetAttribute(k_clique_big<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clique_big<K>, kThreads, smem);
         int bb = sms * (per_sm > 0 ? per_sm : 1);
-        if (nroots < bb) bb = (int)std::max<int64_t>(1, nroots);
-        k_clique_big<K><<<bb, kThreads, smem, s>>>(v.dag_rp, v.dag_col, lo, hi, mo, d_work + 1, d_count);
+        const int64_t slots = (int64_t)ent.size() + (nroots + kBigPop - 1) / kBigPop;
+        if (slots < bb) bb = (int)std::max<int64_t>(1, slots);
+        k_clique_big<K><<<bb, kThreads, smem, s>>>(v.dag_rp, v.dag_col, lo, hi, mo, heavy_d, d_ent,
+                                                    (int)ent.size(), grows, d_work + 1, d_count);
         GZ_COUNT_LAUNCH();
     }
-    cudaError_t e = cudaGetLastError();
+    if (d_ent) cudaFreeAsync(d_ent, s);
+    if (grows) cudaFreeAsync(grows, s);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "clique launch");
     return GZ_OK;
 }
@@ -279,7 +496,7 @@ gz_status launch_k(const GzView& v, int64_t lo, int64_t hi, cudaStream_t s, unsi
 }  // namespace
 
 bool clique_eligible(const GzProg& p, const gz_plan& plan, const GzView& v) {
-    if (plan.k < 4 || plan.k > 8 || !v.has_dag || v.max_out > kCliqueMaxOut) return false;
+    if (plan.k < 4 || plan.k > 8 || !v.has_dag) return false;
     for (int i = 0; i < plan.k; ++i)
         for (int j = 0; j < plan.k; ++j)
             if (i != j && !plan.adj[i * plan.k + j]) return false;
@@ -289,16 +506,18 @@ bool clique_eligible(const GzProg& p, const gz_plan& plan, const GzView& v) {
     return true;
 }
 
-// d_count must be zeroed; d_work holds two zeroed counters.
-gz_status clique_launch(int k, const GzView& v, int64_t lo, int64_t hi, cudaStream_t s,
+// Adds the cliques of the roots in [lo, hi) whose out-list holds at most
+// kCliqueMaxOut vertices to *d_count; longer roots are left to the caller.
+// d_work holds two zeroed counters.
+gz_status clique_launch(int k, const GzView& v, int64_t n, int64_t lo, int64_t hi, cudaStream_t s,
                         unsigned long long* d_count, unsigned long long* d_work) {
     if (hi <= lo) return GZ_OK;
     switch (k) {
-        case 4: return launch_k<4>(v, lo, hi, s, d_count, d_work);
-        case 5: return launch_k<5>(v, lo, hi, s, d_count, d_work);
-        case 6: return launch_k<6>(v, lo, hi, s, d_count, d_work);
-        case 7: return launch_k<7>(v, lo, hi, s, d_count, d_work);
-        case 8: return launch_k<8>(v, lo, hi, s, d_count, d_work);
+        case 4: return launch_k<4>(v, n, lo, hi, s, d_count, d_work);
+        case 5: return launch_k<5>(v, n, lo, hi, s, d_count, d_work);
+        case 6: return launch_k<6>(v, n, lo, hi, s, d_count, d_work);
+        case 7: return launch_k<7>(v, n, lo, hi, s, d_count, d_work);
+        case 8: return launch_k<8>(v, n, lo, hi, s, d_count, d_work);
     }
     set_error("clique kernel: k = %d unsupported", k);
     return GZ_EINVAL;

@@ -28,8 +28,10 @@ namespace gz {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kStageWords = 1024;                      // per-warp shared staging (int32)
-constexpr int kWarpSmemWords = kStageWords + 64 + 64;  // + lane offsets, lengths, list pointers
+constexpr int kStageWords = 1024;  // per-warp shared staging of a fixed operand (int32)
+constexpr int kHashSlots = 2048;   // per-warp open-addressing hash set of that operand
+// per warp: staged operand, lane offsets, lengths, list pointers, hash set
+constexpr int kWarpSmemWords = kStageWords + 64 + 64 + kHashSlots;
 
 // Per-query descriptor in device memory.
 struct KQ {
@@ -44,6 +46,8 @@ struct KQ {
     int64_t unit_lo;       // first unit (edge index) of this query
     int64_t unit_begin;    // offset of this query in the launch's unit space
     int64_t unit_count;
+    int64_t min_root_out;  // > 0: units whose root has a shorter out-list are skipped
+    int32_t out_slot;      // count slot of this query
     int64_t buf_off[GZ_MAXBUF];
     int64_t buf_cap[GZ_MAXBUF];
 };
@@ -237,6 +241,34 @@ __device__ __forceinline__ bool excluded(uint8_t mask, const WarpState& ws, int3
     return ex;
 }
 
+// Open-addressing hash set of distinct non-negative ids in shared memory
+// (kHashSlots slots, -1 = empty, linear probing). At most kStageWords keys, so
+// the load factor stays <= 1/2 and every probe ends at an empty slot.
+__device__ __forceinline__ uint32_t hash_slot(int32_t x) {
+    return ((uint32_t)x * 0x9E3779B1u) >> (32 - 11);
+}
+
+__device__ __forceinline__ void hash_build(int32_t* H, const int32_t* F, int64_t nF, int lane) {
+    for (int i = lane; i < kHashSlots; i += 32) H[i] = -1;
+    __syncwarp();
+    for (int64_t i = lane; i < nF; i += 32) {
+        const int32_t x = F[i];
+        uint32_t s = hash_slot(x);
+        while (atomicCAS(&H[s], -1, x) != -1) s = (s + 1) & (kHashSlots - 1);
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ bool hash_has(const int32_t* H, int32_t x) {
+    uint32_t s = hash_slot(x);
+    for (;;) {
+        const int32_t v = H[s];
+        if (v == x) return true;
+        if (v < 0) return false;
+        s = (s + 1) & (kHashSlots - 1);
+    }
+}
+
 // The last loop, flattened over every candidate c of loop k-2. The one count
 // operation of loop k-2 reads N(c) and otherwise only sets fixed for this call:
 //  shape 1: |F[<b_c] op N(c)[<b_c]| with F fixed (the left operand);
@@ -257,6 +289,8 @@ __device__ void last_level_flat(const KQ& q, const GzOp& op, WarpState& ws, List
     const int32_t** rptr = reinterpret_cast<const int32_t**>(sm + kStageWords + 64);
     const int32_t* F = nullptr;
     int64_t nF = 0;
+    int32_t* H = sm + kStageWords + 128;
+    bool hashed = false;
     const bool sub = !shape2 && op.right_sub[0] != 0;
     const bool bounded = op.bound_pos >= 0;
     if (!shape2) {
@@ -273,6 +307,11 @@ __device__ void last_level_flat(const KQ& q, const GzOp& op, WarpState& ws, List
             for (int64_t i = lane; i < nF; i += 32) sm[i] = F[i];
             __syncwarp();
             F = sm;
+            // probes of F are then O(1) hash lookups instead of binary searches
+            if (S.n >= 2 && nF >= 16) {
+                hash_build(H, F, nF, lane);
+                hashed = true;
+            }
         }
     }
     const int sdag = shape2 ? op.left_dag : op.right_dag[0];
@@ -309,7 +348,10 @@ __device__ void last_level_flat(const KQ& q, const GzOp& op, WarpState& ws, List
                     if (e < beta && in_sorted(F, Lc, e) && !in_sorted(R, m, e)) acc -= 1ull;
                 }
         }
-        const bool dirA = valid && (shape2 || m <= Lc);
+        // A streams N(c) and probes F (a hash lookup when F is hashed); B streams
+        // F and binary-searches N(c) in global memory, several dependent loads
+        // per element, so with a hashed F A is taken up to 8x the length of B
+        const bool dirA = valid && (shape2 || m <= (hashed ? 8 * Lc : Lc));
         const bool dirB = valid && !dirA;
         for (int pass = 0; pass < 2; ++pass) {
             const bool mine = pass == 0 ? dirA : dirB;
@@ -330,7 +372,7 @@ __device__ void last_level_flat(const KQ& q, const GzOp& op, WarpState& ws, List
             for (int64_t f = lane; f < total; f += 32) {
                 int lo = 0, hi = 31;  // first lane whose inclusive offset exceeds f
                 while (lo < hi) {
-                    int mid = (lo + hi) >> 1;
+                    const int mid = (lo + hi) >> 1;
                     if (offs[mid] > f) hi = mid; else lo = mid + 1;
                 }
                 const int64_t i = f - (lo ? offs[lo - 1] : 0);
@@ -347,7 +389,7 @@ __device__ void last_level_flat(const KQ& q, const GzOp& op, WarpState& ws, List
                         if (keep && !excluded(xm, ws, x)) acc += 1ull;
                         continue;
                     }
-                    found = in_sorted(F, nF, x);
+                    found = hashed ? hash_has(H, x) : in_sorted(F, nF, x);
                 } else {
                     x = F[i];
                     found = contains(rptr[lo], lens[lo], x);
@@ -366,6 +408,7 @@ __device__ void process_unit(const KQ& q, int64_t unit, WarpState& ws, int32_t* 
     const GzProg& P = q.prog;
     const int k = P.k;
     const int32_t e0 = q.usrc[unit];
+    if (q.min_root_out > 0 && q.drp[e0 + 1] - q.drp[e0] < q.min_root_out) return;
     const int32_t e1 = q.ucol[unit];
     ws.emb[0] = e0;
     ws.emb[1] = e1;
@@ -448,7 +491,7 @@ __global__ void __launch_bounds__(256, 2) k_enumerate(const KQ* __restrict__ qs,
             if (cur < 0 || u < qs[cur].unit_begin || u >= qs[cur].unit_begin + qs[cur].unit_count) {
                 if (cur >= 0) {
                     unsigned long long s = warp_sum(acc);
-                    if (lane == 0 && s) atomicAdd(&counts[cur], s);
+                    if (lane == 0 && s) atomicAdd(&counts[qs[cur].out_slot], s);
                     acc = 0;
                 }
                 int lo = 0, hi = nq - 1;  // last query with unit_begin <= u
@@ -464,7 +507,7 @@ __global__ void __launch_bounds__(256, 2) k_enumerate(const KQ* __restrict__ qs,
     }
     if (cur >= 0) {
         unsigned long long s = warp_sum(acc);
-        if (lane == 0 && s) atomicAdd(&counts[cur], s);
+        if (lane == 0 && s) atomicAdd(&counts[qs[cur].out_slot], s);
     }
 }
 
@@ -508,6 +551,8 @@ void fill_kq(const Query& Q, KQ& k, uint64_t* words_out) {
     else { k.usrc = v.src; k.ucol = v.col; k.urp = v.rp; }
     k.unit_lo = Q.unit_lo;
     k.unit_count = Q.unit_hi - Q.unit_lo;
+    k.min_root_out = Q.min_root_out;
+    k.out_slot = 0;
     uint64_t off = 0;
     for (int b = 0; b < Q.prog->nbuf; ++b) {
         uint64_t cap = (uint64_t)(Q.prog->buf_dag[b] ? v.max_out : Q.g->max_deg);
@@ -536,6 +581,12 @@ gz_status count_one_in_region(const Query& Q, const LaunchCfg& cfg, cudaStream_t
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int bw = cfg.block_warps;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_enumerate_one, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             8 * kWarpSmemWords * 4);
+        attr = true;
+    }
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate_one, bw * 32, bw * kWarpSmemWords * 4);
     if (per_sm < 1) per_sm = 1;
     int64_t warps = (int64_t)sms * per_sm * bw;
@@ -619,6 +670,8 @@ gz_status count_launch(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream
         k.unit_lo = Q.unit_lo;
         k.unit_count = Q.unit_hi - Q.unit_lo;
         k.unit_begin = total;
+        k.min_root_out = Q.min_root_out;
+        k.out_slot = Q.out_slot >= 0 ? Q.out_slot : i;
         total += k.unit_count;
         uint64_t off = 0;
         for (int b = 0; b < Q.prog->nbuf; ++b) {

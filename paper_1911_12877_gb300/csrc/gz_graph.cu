@@ -568,6 +568,8 @@ gz_status orient(gz_graph* g, cudaStream_t s) {
             cudaFree(o.dag_rp); cudaFree(o.dag_col); cudaFree(o.dag_src);
             o.dag_rp = nullptr; o.dag_col = nullptr; o.dag_src = nullptr;
             o.has_dag = false;
+            o.heavy.clear();
+            o.heavy_built = false;
         }
         if (o.src) { cudaFree(o.src); o.src = nullptr; }
         st = build_dag(g, &o, s);

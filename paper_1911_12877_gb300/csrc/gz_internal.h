@@ -3,6 +3,8 @@
 #pragma once
 #include <stdint.h>
 #include <atomic>
+#include <utility>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "../../include/gz.h"
@@ -79,6 +81,10 @@ struct GzView {
     int64_t max_out = 0;
     bool owned_csr = true;
     bool has_dag = false;
+    // roots whose out-list is long enough that the clique kernels split them
+    // over several CTAs: (root, out-degree) pairs, gathered once per DAG build
+    std::vector<std::pair<int32_t, int32_t>> heavy;
+    bool heavy_built = false;
 };
 
 struct gz_graph {
@@ -110,6 +116,10 @@ struct Query {
     const gz_graph* g;
     const GzView* view;
     int64_t unit_lo, unit_hi;  // work units (edges of the unit CSR) in this launch
+    const gz_plan* plan = nullptr;
+    int64_t root_lo = 0, root_hi = -1;  // the roots those units belong to (hi < 0: n)
+    int64_t min_root_out = 0;  // > 0: only roots with at least this out-degree
+    int out_slot = -1;         // count slot in the launch's count array (-1: its index)
 };
 struct LaunchCfg {
     int block_warps = 8;  // warps per CTA
@@ -130,7 +140,16 @@ gz_status count_one_in_region(const Query& Q, const LaunchCfg& cfg, cudaStream_t
 // clique side (gz_clique.cu): oriented k-cliques as bitsets over the root's out-list
 constexpr int kCliqueMaxOut = 1024;  // largest out-list kept in shared memory
 bool clique_eligible(const GzProg& p, const gz_plan& plan, const GzView& v);
-gz_status clique_launch(int k, const GzView& v, int64_t lo, int64_t hi, cudaStream_t s,
+// Enqueues nq queries on stream s: oriented cliques on the bitset kernels (their
+// roots with out-lists longer than kCliqueMaxOut on the general kernel), the rest
+// in one persistent general launch. Query i adds its count to d_counts[i];
+// d_work holds 2 zeroed counters per query; scratch as for count_launch.
+gz_status launch_mixed(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream_t s,
+                       unsigned long long* d_counts, int* d_status, unsigned long long* d_work,
+                       void* scratch, uint64_t scratch_bytes);
+// Scratch bytes launch_mixed needs for these queries.
+uint64_t mixed_scratch_bytes(const Query* qs, int nq, const LaunchCfg& cfg);
+gz_status clique_launch(int k, const GzView& v, int64_t n, int64_t lo, int64_t hi, cudaStream_t s,
                         unsigned long long* d_count, unsigned long long* d_work);
 
 }  // namespace gz

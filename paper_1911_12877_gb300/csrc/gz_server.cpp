@@ -97,19 +97,19 @@ gz_status launch_batch(gz_server* s, Slot& sl) {
         gz_status st = prepare_query(r->plan, r->graph, r->ori, 0, -1, sl.stream, qs[i]);
         if (st != GZ_OK) return st;
     }
-    uint64_t words = 0;
-    for (int i = 0; i < nq; ++i)
-        words = std::max(words, scratch_words_per_warp(*qs[i].prog, *qs[i].g, *qs[i].view));
-    const uint64_t need = (uint64_t)resident_warps(kCfg) * words * 4 + 256;
+    const uint64_t need = mixed_scratch_bytes(qs.data(), nq, kCfg) + 256;
+    // counts [nq], status, clique work counters [2 nq]
+    const size_t words = (size_t)nq + 1 + 2 * (size_t)nq;
     void* scratch = nullptr;
     unsigned long long* d = nullptr;
     cudaError_t e = cudaMallocAsync(&scratch, need, sl.stream);
-    if (e == cudaSuccess) e = cudaMallocAsync(&d, sizeof(unsigned long long) * (nq + 1), sl.stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d, sizeof(unsigned long long) * words, sl.stream);
     if (e != cudaSuccess) return cuda_fail(e, "server: scratch");
-    e = cudaMemsetAsync(d, 0, sizeof(unsigned long long) * (nq + 1), sl.stream);
+    e = cudaMemsetAsync(d, 0, sizeof(unsigned long long) * words, sl.stream);
     gz_status st = e == cudaSuccess ? GZ_OK : cuda_fail(e, "server: memset");
     if (st == GZ_OK)
-        st = count_launch(qs.data(), nq, kCfg, sl.stream, d, scratch, need, reinterpret_cast<int*>(d + nq));
+        st = launch_mixed(qs.data(), nq, kCfg, sl.stream, d, reinterpret_cast<int*>(d + nq), d + nq + 1,
+                          scratch, need);
     if (st == GZ_OK) {
         e = cudaMemcpyAsync(sl.h_counts, d, sizeof(unsigned long long) * (nq + 1), cudaMemcpyDeviceToHost, sl.stream);
         if (e != cudaSuccess) st = cuda_fail(e, "server: copy back");

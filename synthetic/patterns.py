@@ -74,33 +74,34 @@ def adjacency(name_or_edges, k: int | None = None) -> np.ndarray:
     return a
 
 
-def batch_queries(n_graphs: int = 16, per_graph: int = 4, seed: int = 4, small_scales=None):
+#: largest R-MAT scale a pattern is placed on in the batched workload. The
+#: difference-heavy sparse patterns cost about the sum of cubed degrees on hub
+#: vertices; chordal cycles and K6 have counts of 10^12 and more on the
+#: skewed graphs above these scales, each costing seconds to minutes alone.
+BATCH_MAX_SCALE = {"wedge": 14, "path4": 14, "star3": 14, "c4": 14, "paw": 14, "chordal6": 13,
+                   "chordal5": 16, "k6": 16, "diamond": 18, "k5": 18, "triangle": 21, "k4": 21}
+
+
+def batch_queries(scales=None, per_graph: int = 4, seed: int = 4):
     """Query table of the batched workload: (graph index, pattern name) pairs.
 
-    ``per_graph`` queries per graph (64 in all), every pattern of BATCH_PATTERNS at
-    least four times, and the difference-heavy sparse patterns only on the graphs
-    listed in ``small_scales`` (indices of graphs of R-MAT scale <= 14), because
-    their induced enumeration on hub vertices costs about the sum of cubed degrees.
-    Seeded; the table is an input, not a result.
+    ``per_graph`` queries on each graph (64 in all for the 16 graphs), every
+    pattern of BATCH_PATTERNS at least four times, each only on graphs whose
+    scale is at most BATCH_MAX_SCALE[pattern]. Seeded; the table is an input,
+    not a result.
     """
+    if scales is None:
+        scales = [10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 12, 14, 16, 18]
     rng = np.random.default_rng(seed)
-    small = sorted(small_scales) if small_scales is not None else [0, 1, 2, 3, 4, 12, 13]
-    slots = [(g, j) for g in range(n_graphs) for j in range(per_graph)]
-    small_slots = [s for s in slots if s[0] in small]
-    big_slots = [s for s in slots if s[0] not in small]
+    slots = [(g, j) for g in range(len(scales)) for j in range(per_graph)]
     table = {}
-    sparse = [p for p in BATCH_PATTERNS if p in BATCH_SPARSE]
-    dense = [p for p in BATCH_PATTERNS if p not in BATCH_SPARSE]
-    order = rng.permutation(len(small_slots))
-    need = [p for p in sparse for _ in range(4)]
-    for p, i in zip(need, order):
-        table[small_slots[i]] = p
-    free = [small_slots[i] for i in order[len(need):]] + big_slots
-    free = [free[i] for i in rng.permutation(len(free))]
-    need = [p for p in dense for _ in range(4)]
-    for p, s in zip(need, free):
-        table[s] = p
-    for s in free[len(need):]:
-        pool = BATCH_PATTERNS if s[0] in small else dense
-        table[s] = pool[int(rng.integers(len(pool)))]
+    # most constrained patterns first, four copies each, into random eligible slots
+    for p in sorted(BATCH_PATTERNS, key=lambda x: (BATCH_MAX_SCALE[x], x)):
+        for _ in range(4):
+            free = [s for s in slots if s not in table and scales[s[0]] <= BATCH_MAX_SCALE[p]]
+            table[free[int(rng.integers(len(free)))]] = p
+    for s in slots:
+        if s not in table:
+            pool = [p for p in BATCH_PATTERNS if scales[s[0]] <= BATCH_MAX_SCALE[p]]
+            table[s] = pool[int(rng.integers(len(pool)))]
     return [(g, table[(g, j)]) for g, j in slots]

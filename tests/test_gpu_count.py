@@ -272,5 +272,35 @@ def test_patterns_rmat22_sampled():
     G = gz.Graph.from_csr(g).orient()
     for name, rec in gold["patterns"].items():
         p = gz.Plan(name)
-        for (lo, hi, c) in rec["samples"]:
+        for (lo, hi, c, *_) in rec["samples"]:
             assert gz.count(p, G, True, lo, hi) == c, (name, lo, hi)
+
+
+@pytest.mark.parametrize("k", [4, 5, 6, 7, 8])
+def test_cliques_on_long_out_lists(k):
+    """Oriented k-cliques through the bitset kernels on roots whose out-lists span
+    several 32-bit words (odd and even word counts) against the oracle."""
+    for n, p, seed in [(90, 0.55, 41), (160, 0.45, 42), (240, 0.42, 44), (300, 0.4, 43)]:
+        g = S.random_small(n, p, seed)
+        G = gz.Graph.from_csr(g).orient()
+        assert G.info()["max_out_degree_oriented"] > 32
+        name = {4: "k4", 5: "k5", 6: "k6"}.get(k)
+        a = adjacency(name) if name else adjacency([(i, j) for i in range(k) for j in range(i + 1, k)], k)
+        want = oracle_count(a, g)
+        assert gz.count(gz.Plan(a), G, orientation=True) == want, (k, n)
+
+
+def test_cliques_with_out_lists_beyond_the_bitset_limit():
+    """Roots whose out-list exceeds the bitset kernels' 1024 are counted by the
+    general kernel in the same call. K_{m,m} plus a perfect matching inside each
+    side: every K4 takes one matching edge per side, so there are (m/2)^2 of
+    them, and there is no K5 (a side holds no triangle)."""
+    m = 1100
+    e = [(i, m + j) for i in range(m) for j in range(m)]
+    e += [(2 * i, 2 * i + 1) for i in range(m // 2)] + [(m + 2 * i, m + 2 * i + 1) for i in range(m // 2)]
+    g = S.from_edges(2 * m, e, "Kmm_matchings")
+    G = gz.Graph.from_csr(g).orient()
+    assert G.info()["max_out_degree_oriented"] > 1024
+    assert gz.count(gz.Plan("k4"), G, orientation=True) == (m // 2) ** 2
+    assert gz.count(gz.Plan("k5"), G, orientation=True) == 0
+    assert gz.count(gz.Plan("k4"), G, orientation=True) == oracle_count("k4", g)
