@@ -64,40 +64,107 @@ def clique():
     _dump("clique_rmat20.json", rec)
 
 
-# Root ranges (reindexed ids) of the arbitrary-pattern workload: a top hub block, two
-# mid-degree blocks and a low-degree block. Each range is grown from width 1 by
-# doubling while the oracle stays within a few seconds on it, so the sample costs
-# the same order of CPU time whatever the pattern.
-PATTERN_STARTS = [64, 20000, 300000, 1000000]
+# Root ranges (reindexed ids) of the arbitrary-pattern workload, from hub blocks
+# down to low-degree blocks. Each range starts at width 1 and doubles while one
+# oracle run stays under SAMPLE_S seconds; a run that passes ATTEMPT_S is
+# stopped and the previous width kept (a start whose first root alone passes it
+# is dropped), so every pattern's sample costs minutes of CPU at most. Each
+# sample stores [lo, hi, count, E].
+PATTERN_STARTS = [64, 1000, 20000, 100000, 300000, 1000000]
+# the house costs the oracle minutes for one root of degree 40 on this graph
+# (its only restriction is one pair), so its blocks start lower in degree
+PATTERN_STARTS_BY_NAME = {"house": [600000, 800000, 1000000, 1300000, 1600000, 2000000]}
 PATTERN_MAX_W = 4096
+SAMPLE_S = 3.0
+ATTEMPT_S = 90.0
 
 
-def patterns():
+class _Worker:
+    """A spawned process that holds the reindexed graph and runs oracle counts,
+    so one that runs past ATTEMPT_S can be stopped (OpenMP state does not
+    survive a fork, hence spawn and a graph file instead of inheritance)."""
+
+    def __init__(self, path):
+        import multiprocessing as mp
+        self.path = path
+        self.ctx = mp.get_context("spawn")
+        self._start()
+
+    def _start(self):
+        self.parent, child = self.ctx.Pipe()
+        self.proc = self.ctx.Process(target=_worker_main, args=(child, self.path), daemon=True)
+        self.proc.start()
+
+    def count(self, a, order, lo, hi):
+        self.parent.send((a, order, lo, hi))
+        if self.parent.poll(ATTEMPT_S):
+            return self.parent.recv()
+        self.proc.kill()
+        self.proc.join()
+        self._start()
+        return None
+
+    def close(self):
+        self.proc.kill()
+        self.proc.join()
+
+
+def _worker_main(conn, path):
+    import numpy as np
+    z = np.load(path)
+    go = S.Csr(int(z["n"]), z["row_ptr"], z["col"], "reindexed")
+    while True:
+        a, order, lo, hi = conn.recv()
+        c, e = O.count_nested(a, order, go, lo, hi)
+        conn.send((int(c), int(e)))
+
+
+def patterns(names=None):
+    """Recomputes the samples of `names` (default: all five) and keeps the other
+    patterns' stored records."""
+    import numpy as np
+    import tempfile
     g = S.rmat_patterns()
     go, _ = O.reindex(g)
+    tmp = os.path.join(tempfile.mkdtemp(), "go.npz")
+    np.savez(tmp, n=go.n, row_ptr=go.row_ptr, col=go.col)
+    worker = _Worker(tmp)
     rec = {"graph": g.name, "n": g.n, "nnz": g.nnz, "oriented": True, "patterns": {}}
-    for name in PATTERN_SET:
+    path = os.path.join(HERE, "patterns_rmat22.json")
+    if names and os.path.exists(path):
+        old = json.load(open(path))
+        if old.get("nnz") == g.nnz:
+            rec["patterns"] = old["patterns"]
+    for name in (names or PATTERN_SET):
         a, order = _plan(name)
         t0 = time.time()
         samples = []
-        for s in PATTERN_STARTS:
+        for s in PATTERN_STARTS_BY_NAME.get(name, PATTERN_STARTS):
             w, last = 1, None
-            while True:
+            while w <= PATTERN_MAX_W:
                 t = time.time()
-                c = O.count_nested(a, order, go, s, s + w)[0]
+                r = worker.count(a, order, s, s + w)
                 dt = time.time() - t
-                last = [s, s + w, c]
-                if dt > 4.0 or w >= PATTERN_MAX_W:
+                if r is None:
+                    break
+                last = [s, s + w, r[0], r[1]]
+                if dt > SAMPLE_S:
                     break
                 w *= 2
-            samples.append(last)
+            if last is not None:
+                samples.append(last)
         rec["patterns"][name] = {"order": order, "samples": samples,
                                  "oracle_s": round(time.time() - t0, 1)}
         print(name, rec["patterns"][name], flush=True)
+    worker.close()
+    os.remove(tmp)
     _dump("patterns_rmat22.json", rec)
 
 
 if __name__ == "__main__":
     which = sys.argv[1:] or ["triangle", "clique", "patterns"]
     for w in which:
-        globals()[w]()
+        if w.startswith("patterns:"):  # e.g. patterns:house
+            patterns(w.split(":", 1)[1].split(","))
+        else:
+            globals()[w]()
