@@ -181,7 +181,7 @@ uint64_t mixed_scratch_bytes(const Query* qs, int nq, const LaunchCfg& cfg) {
     uint64_t words = 0;
     for (int i = 0; i < nq; ++i) {
         const Query& q = qs[i];
-        if (q.plan && clique_eligible(*q.prog, *q.plan, *q.view) && q.view->max_out <= kCliqueMaxOut)
+        if (q.plan && clique_eligible(*q.prog, *q.plan, *q.view) && q.view->max_out <= kCliqueLongOut)
             continue;
         words = std::max(words, scratch_words_per_warp(*q.prog, *q.g, *q.view));
     }
@@ -200,10 +200,10 @@ gz_status launch_mixed(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream
             const int64_t lo = q.root_lo < 0 ? 0 : q.root_lo;
             const int64_t hi = (q.root_hi < 0 || q.root_hi > q.g->n) ? q.g->n : q.root_hi;
             gz_status st = clique_launch(q.plan->k, *q.view, q.g->n, lo, hi, s, d_counts + i,
-                                         d_work + 2 * i);
+                                         d_work + 3 * i);
             if (st != GZ_OK) return st;
-            if (q.view->max_out <= kCliqueMaxOut) continue;
-            q.min_root_out = kCliqueMaxOut + 1;  // roots the bitset kernels leave out
+            if (q.view->max_out <= kCliqueLongOut) continue;
+            q.min_root_out = kCliqueLongOut + 1;  // roots the bitset kernels leave out
         }
         gen.push_back(q);
     }
@@ -219,8 +219,8 @@ gz_status run_queries(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream_
     std::lock_guard<std::mutex> lk(a.mu);
     gz_status st = arena_reserve(a, need);
     if (st != GZ_OK) return st;
-    // counts [nq], status, clique work counters [2 nq]
-    const size_t words = (size_t)nq + 1 + 2 * (size_t)nq;
+    // counts [nq], status, clique work counters [3 nq]
+    const size_t words = (size_t)nq + 1 + 3 * (size_t)nq;
     unsigned long long* d = nullptr;
     cudaError_t e = cudaMallocAsync(&d, sizeof(unsigned long long) * words, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync counts");
@@ -371,6 +371,7 @@ void gz_graph_destroy(gz_graph* g) {
     auto free_view = [](GzView& v, bool csr) {
         if (csr) { cudaFree(v.rp); cudaFree(v.col); }
         cudaFree(v.dag_rp); cudaFree(v.dag_col); cudaFree(v.dag_src); cudaFree(v.src);
+        cudaFree(v.heavy_rows);
     };
     cudaDeviceSynchronize();
     free_view(g->orig, g->orig.owned_csr);

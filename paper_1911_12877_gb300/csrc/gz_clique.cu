@@ -30,8 +30,10 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kThreads = 256;
 constexpr int kBigPop = 16;     // roots per queue slot of the big kernel; most are skipped
+constexpr int kBigThreads = 512;  // threads of a big-kernel CTA (one root at a time)
 constexpr int kHeavyD = 128;    // out-degree from which a root is split over several CTAs
 constexpr uint64_t kHeavyRowWords = 1ull << 29;  // budget for prebuilt heavy rows (2 GiB)
+constexpr uint64_t kLongRowWords = 1ull << 30;   // budget for long roots' global rows (4 GiB)
 
 __device__ __forceinline__ bool has(const int32_t* __restrict__ R, int n, int32_t x) {
     int lo = 0, len = n;
@@ -150,13 +152,15 @@ __global__ void __launch_bounds__(kThreads) k_clique_small(const int64_t* __rest
 
 // Builds row(a), a in [1, d), of the root whose out-list O[0, d) is in shared
 // memory into rows (stride Ws, zeroed): one warp per a streams the shorter of
-// O[0, a) and N'(O[a]) and looks each element up in the other (a binary search
-// in shared memory, or in the global out-list), so a root costs about
-// sum_a min(a, |N'(O[a])|) lookups.
+// O[0, a) and N'(O[a]) and looks each element up in the other, so a root costs
+// about sum_a min(a, |N'(O[a])|) lookups. Lookups in O are binary searches in
+// shared memory; lookups in N'(O[a]) are too when stage (per warp, kCliqueMaxOut
+// words, or NULL) is given: the warp first copies N'(O[a]) there (coalesced),
+// else they are binary searches in global memory.
 __device__ __forceinline__ void build_rows(const int64_t* __restrict__ drp,
                                            const int32_t* __restrict__ dcol, const int32_t* O,
                                            int d, uint32_t* rows, int Ws, int lane, int warp,
-                                           int nwarps) {
+                                           int nwarps, int32_t* stage) {
     for (int a = warp + 1; a < d; a += nwarps) {
         const int32_t u = O[a];
         const int64_t ub = drp[u];
@@ -167,6 +171,16 @@ __device__ __forceinline__ void build_rows(const int64_t* __restrict__ drp,
                 const int b = index_of(O, a, __ldg(dcol + ub + i));
                 if (b >= 0) atomicOr(ra + (b >> 5), 1u << (b & 31));
             }
+        } else if (stage && du <= kCliqueMaxOut) {
+            for (int i = lane; i < du; i += 32) stage[i] = __ldg(dcol + ub + i);
+            __syncwarp();
+            for (int b0 = 0; b0 < a; b0 += 32) {
+                const int b = b0 + lane;
+                const bool in = b < a && index_of(stage, du, O[b]) >= 0;
+                const uint32_t m = __ballot_sync(kFull, in);
+                if (lane == 0) ra[b0 >> 5] = m;
+            }
+            __syncwarp();
         } else {
             for (int b0 = 0; b0 < a; b0 += 32) {
                 const int b = b0 + lane;
@@ -192,6 +206,7 @@ __global__ void __launch_bounds__(kThreads) k_clique_rows(const int64_t* __restr
     uint32_t* rows = sm;
     int32_t* O = reinterpret_cast<int32_t*>(sm + (size_t)max_out * Wsmax);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t* stage = O + max_out + (size_t)warp * kCliqueMaxOut;
     for (int h = blockIdx.x; h < nh; h += gridDim.x) {
         const int64_t v = hr[h].x;
         const int64_t ob = drp[v];
@@ -200,7 +215,7 @@ __global__ void __launch_bounds__(kThreads) k_clique_rows(const int64_t* __restr
         for (int i = threadIdx.x; i < d; i += kThreads) O[i] = dcol[ob + i];
         for (int i = threadIdx.x; i < d * Ws; i += kThreads) rows[i] = 0;
         __syncthreads();
-        build_rows(drp, dcol, O, d, rows, Ws, lane, warp, kThreads / 32);
+        build_rows(drp, dcol, O, d, rows, Ws, lane, warp, kThreads / 32, stage);
         __syncthreads();
         uint32_t* dst = grows + (uint32_t)hr[h].z;
         for (int i = threadIdx.x; i < d * Ws; i += kThreads) dst[i] = rows[i];
@@ -219,9 +234,9 @@ __global__ void __launch_bounds__(kThreads) k_clique_rows(const int64_t* __restr
 // finds its (a, b) and runs the remaining K - 3 loops over row(a) & row(b).
 // Consecutive threads take consecutive edges (same a, neighbouring b), so row(a)
 // reads are broadcasts and row(b) reads fall in distinct banks. A heavy root's
-// parts take interleaved blocks of kThreads edges.
+// parts take interleaved blocks of kBigThreads edges.
 template <int K>
-__global__ void __launch_bounds__(kThreads) k_clique_big(const int64_t* __restrict__ drp,
+__global__ void __launch_bounds__(kBigThreads) k_clique_big(const int64_t* __restrict__ drp,
                                                          const int32_t* __restrict__ dcol,
                                                          int64_t root_lo, int64_t root_hi,
                                                          int max_out, int heavy_d,
@@ -231,14 +246,14 @@ __global__ void __launch_bounds__(kThreads) k_clique_big(const int64_t* __restri
                                                          unsigned long long* __restrict__ work,
                                                          unsigned long long* __restrict__ count) {
     extern __shared__ uint32_t sm[];
-    __shared__ unsigned long long red[kThreads / 32];
+    __shared__ unsigned long long red[kBigThreads / 32];
     __shared__ int64_t s_root;
     const int Wsmax = ((max_out + 31) >> 5) | 1;
     uint32_t* rows = sm;
     int32_t* O = reinterpret_cast<int32_t*>(sm + (size_t)max_out * Wsmax);
     int32_t* pre = O + max_out;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = kThreads / 32;
+    const int nwarps = kBigThreads / 32;
     unsigned long long acc = 0;
     const int64_t nchunks = (root_hi - root_lo + kBigPop - 1) / kBigPop;
     for (;;) {
@@ -270,14 +285,14 @@ __global__ void __launch_bounds__(kThreads) k_clique_big(const int64_t* __restri
         const int d = (int)(drp[v + 1] - ob);
         if (d <= 32 || d > max_out || (slot >= nheavy && d >= heavy_d)) continue;
         const int Ws = ((d + 31) >> 5) | 1;
-        for (int i = threadIdx.x; i < d; i += kThreads) O[i] = dcol[ob + i];
+        for (int i = threadIdx.x; i < d; i += kBigThreads) O[i] = dcol[ob + i];
         if (src) {
-            for (int i = threadIdx.x; i < d * Ws; i += kThreads) rows[i] = __ldg(src + i);
+            for (int i = threadIdx.x; i < d * Ws; i += kBigThreads) rows[i] = __ldg(src + i);
             __syncthreads();
         } else {
-            for (int i = threadIdx.x; i < d * Ws; i += kThreads) rows[i] = 0;
+            for (int i = threadIdx.x; i < d * Ws; i += kBigThreads) rows[i] = 0;
             __syncthreads();
-            build_rows(drp, dcol, O, d, rows, Ws, lane, warp, nwarps);
+            build_rows(drp, dcol, O, d, rows, Ws, lane, warp, nwarps, nullptr);
             __syncthreads();
         }
         // pre[a] = number of local edges (a, b), b < a, before row a
@@ -300,8 +315,8 @@ __global__ void __launch_bounds__(kThreads) k_clique_big(const int64_t* __restri
         }
         __syncthreads();
         const int pairs = pre[d];
-        for (int blk = part; blk * kThreads < pairs; blk += parts) {
-            const int p = blk * kThreads + threadIdx.x;
+        for (int blk = part; blk * kBigThreads < pairs; blk += parts) {
+            const int p = blk * kBigThreads + threadIdx.x;
             if (p >= pairs) continue;
             int lo = 0, hi = d - 1;  // last a with pre[a] <= p
             while (lo < hi) {
@@ -326,6 +341,110 @@ __global__ void __launch_bounds__(kThreads) k_clique_big(const int64_t* __restri
         }
         __syncthreads();
       }
+    }
+    unsigned long long s = block_sum(acc, red);
+    if (threadIdx.x == 0 && s) atomicAdd(count, s);
+}
+
+// Roots whose out-list is too long for shared-memory rows (kCliqueMaxOut <
+// |O| <= kCliqueLongOut): rows live in global memory, where k_clique_long_rows
+// builds them (one CTA per root, O in shared memory, rows zeroed by the host),
+// and k_clique_long walks their local DAG edges as k_clique_big does, reading
+// the rows through the L1/L2 caches. lr[i] = (root, part | parts << 16, word
+// offset of the root's rows); the offsets of the build list have parts = 1.
+__global__ void __launch_bounds__(kThreads) k_clique_long_rows(const int64_t* __restrict__ drp,
+                                                               const int32_t* __restrict__ dcol,
+                                                               const int4* __restrict__ lr, int nl,
+                                                               uint32_t* __restrict__ grows) {
+    extern __shared__ uint32_t sm[];
+    int32_t* O = reinterpret_cast<int32_t*>(sm);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int h = blockIdx.x; h < nl; h += gridDim.x) {
+        const int64_t v = lr[h].x;
+        const int64_t ob = drp[v];
+        const int d = (int)(drp[v + 1] - ob);
+        const int Ws = ((d + 31) >> 5) | 1;
+        for (int i = threadIdx.x; i < d; i += kThreads) O[i] = dcol[ob + i];
+        __syncthreads();
+        build_rows(drp, dcol, O, d, grows + (uint32_t)lr[h].z, Ws, lane, warp, kThreads / 32, nullptr);
+        __syncthreads();
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kThreads) k_clique_long(const int64_t* __restrict__ drp,
+                                                          const int4* __restrict__ lr, int nl,
+                                                          const uint32_t* __restrict__ grows,
+                                                          unsigned long long* __restrict__ work,
+                                                          unsigned long long* __restrict__ count) {
+    extern __shared__ uint32_t sm[];
+    int32_t* pre = reinterpret_cast<int32_t*>(sm);  // [kCliqueLongOut + 1]
+    __shared__ unsigned long long red[kThreads / 32];
+    __shared__ int64_t s_slot;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = kThreads / 32;
+    unsigned long long acc = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_slot = (int64_t)atomicAdd(work, 1ull);
+        __syncthreads();
+        const int64_t slot = s_slot;
+        __syncthreads();
+        if (slot >= nl) break;
+        const int4 h = lr[slot];
+        const int part = h.y & 0xffff, parts = h.y >> 16;
+        const int d = (int)(drp[h.x + 1] - drp[h.x]);
+        const int Ws = ((d + 31) >> 5) | 1;
+        const uint32_t* rows = grows + (uint32_t)h.z;
+        // pre[a + 1] = popcount of row a (warp per row), then an inclusive scan
+        for (int a = warp; a < d; a += nwarps) {
+            int c = 0;
+            for (int w = lane, wa = (a + 31) >> 5; w < wa; w += 32) c += __popc(rows[(size_t)a * Ws + w]);
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(kFull, c, o);
+            if (lane == 0) pre[a + 1] = c;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            int run = 0;
+            if (lane == 0) pre[0] = 0;
+            for (int a0 = 1; a0 <= d; a0 += 32) {
+                const int a = a0 + lane;
+                const int c = a <= d ? pre[a] : 0;
+                int incl = c;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                if (a <= d) pre[a] = run + incl;
+                run += __shfl_sync(kFull, incl, 31);
+            }
+        }
+        __syncthreads();
+        const int pairs = pre[d];
+        for (int blk = part; (int64_t)blk * kThreads < pairs; blk += parts) {
+            const int p = blk * kThreads + threadIdx.x;
+            if (p >= pairs) continue;
+            int lo = 0, hi = d - 1;  // last a with pre[a] <= p
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (pre[mid] <= p) lo = mid; else hi = mid - 1;
+            }
+            const int a = lo;
+            int j = p - pre[a];
+            const uint32_t* ra = rows + (size_t)a * Ws;
+            int b = -1;
+            for (int w = 0; w < Ws; ++w) {
+                uint32_t m = ra[w];
+                const int c = __popc(m);
+                if (j < c) {
+                    for (int i = 0; i < j; ++i) m &= m - 1;
+                    b = (w << 5) + __ffs(m) - 1;
+                    break;
+                }
+                j -= c;
+            }
+            acc += count_pair<K>(rows, Ws, a, b);
+        }
+        __syncthreads();
     }
     unsigned long long s = block_sum(acc, red);
     if (threadIdx.x == 0 && s) atomicAdd(count, s);
@@ -398,6 +517,114 @@ int parts_for(int K, int d) {
     return std::max(1, std::min(std::min(p, 64), d));
 }
 
+// Builds, once per out-list view, the bitset rows of every heavy root with at
+// most mo out-neighbours into v.heavy_rows (kept until the view is rebuilt or
+// the graph destroyed). Over kHeavyRowWords words in all, nothing is cached and
+// heavy roots are not split.
+gz_status build_heavy_rows(GzView& v, int mo, int sms, cudaStream_t s) {
+    if (v.heavy_rows_built) return GZ_OK;
+    v.heavy_off.assign(v.heavy.size(), UINT32_MAX);
+    std::vector<int4> list;
+    uint64_t words = 0;
+    for (size_t i = 0; i < v.heavy.size(); ++i) {
+        const int d = v.heavy[i].second;
+        if (d > mo) continue;
+        v.heavy_off[i] = (uint32_t)words;
+        list.push_back(make_int4(v.heavy[i].first, 0, (int)words, 0));
+        words += ((uint64_t)d * (((d + 31) / 32) | 1) + 3) & ~3ull;
+    }
+    v.heavy_rows_built = true;
+    if (list.empty() || words > kHeavyRowWords) {
+        v.heavy_off.assign(v.heavy.size(), UINT32_MAX);
+        return GZ_OK;
+    }
+    int4* d_list = nullptr;
+    cudaError_t e = cudaMalloc(&v.heavy_rows, sizeof(uint32_t) * words);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_list, sizeof(int4) * list.size(), s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_list, list.data(), sizeof(int4) * list.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        const size_t smem = ((size_t)mo * (((mo + 31) / 32) | 1) + mo + (size_t)(kThreads / 32) * kCliqueMaxOut) * 4;
+        cudaFuncSetAttribute(k_clique_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clique_rows, kThreads, smem);
+        const int rb = (int)std::min<size_t>(list.size(), (size_t)sms * std::max(1, per_sm));
+        k_clique_rows<<<rb, kThreads, smem, s>>>(v.dag_rp, v.dag_col, d_list, (int)list.size(), mo,
+                                                 v.heavy_rows);
+        GZ_COUNT_LAUNCH();
+        e = cudaGetLastError();
+    }
+    if (d_list) cudaFreeAsync(d_list, s);
+    if (e != cudaSuccess) {
+        cudaFree(v.heavy_rows);
+        v.heavy_rows = nullptr;
+        v.heavy_off.assign(v.heavy.size(), UINT32_MAX);
+        return cuda_fail(e, "clique: heavy rows");
+    }
+    return GZ_OK;
+}
+
+// Roots of [lo, hi) with kCliqueMaxOut < |O| <= kCliqueLongOut: rows built in
+// global memory (at most kLongRowWords words; roots beyond that budget, and
+// roots longer than kCliqueLongOut, are left to the caller's general kernel,
+// see clique_long_cutoff), then their edges walked by k_clique_long.
+template <int K>
+gz_status launch_long(GzView& v, int64_t lo, int64_t hi, cudaStream_t s,
+                      unsigned long long* d_count, unsigned long long* d_work) {
+    std::vector<std::pair<int32_t, int32_t>> hr;
+    auto it = std::lower_bound(v.heavy.begin(), v.heavy.end(), std::make_pair((int32_t)lo, INT32_MIN));
+    for (; it != v.heavy.end() && it->first < hi; ++it)
+        if (it->second > kCliqueMaxOut && it->second <= kCliqueLongOut) hr.push_back(*it);
+    if (hr.empty()) return GZ_OK;
+    std::stable_sort(hr.begin(), hr.end(), [](const std::pair<int32_t, int32_t>& a,
+                                              const std::pair<int32_t, int32_t>& b) {
+        return a.second > b.second;
+    });
+    std::vector<int4> build, ent;
+    uint64_t words = 0;
+    for (const auto& x : hr) {
+        const uint64_t sz = (uint64_t)x.second * (((x.second + 31) / 32) | 1);
+        if (words + sz > kLongRowWords) break;
+        build.push_back(make_int4(x.first, 1 << 16, (int)words, 0));
+        const int parts = std::min(64, std::max(1, (int)((uint64_t)x.second * x.second / (256 * 256))));
+        for (int p = 0; p < parts; ++p) ent.push_back(make_int4(x.first, p | (parts << 16), (int)words, 0));
+        words += (sz + 3) & ~3ull;
+    }
+    if (build.size() < hr.size()) {
+        set_error("clique: long out-lists exceed the row budget");
+        return GZ_ENOMEM;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int4* d_l = nullptr;
+    uint32_t* grows = nullptr;
+    cudaError_t e = cudaMallocAsync(&d_l, sizeof(int4) * (build.size() + ent.size()), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&grows, sizeof(uint32_t) * words, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(grows, 0, sizeof(uint32_t) * words, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_l, build.data(), sizeof(int4) * build.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_l + build.size(), ent.data(), sizeof(int4) * ent.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        const size_t smem = sizeof(int32_t) * (kCliqueLongOut + 1);
+        cudaFuncSetAttribute(k_clique_long_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_clique_long<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int rb = (int)std::min<size_t>(build.size(), (size_t)sms * 4);
+        k_clique_long_rows<<<rb, kThreads, smem, s>>>(v.dag_rp, v.dag_col, d_l, (int)build.size(), grows);
+        GZ_COUNT_LAUNCH();
+        const int lb = (int)std::min<size_t>(ent.size(), (size_t)sms * 4);
+        k_clique_long<K><<<lb, kThreads, smem, s>>>(v.dag_rp, d_l + build.size(), (int)ent.size(), grows,
+                                                     d_work, d_count);
+        GZ_COUNT_LAUNCH();
+        e = cudaGetLastError();
+    }
+    if (d_l) cudaFreeAsync(d_l, s);
+    if (grows) cudaFreeAsync(grows, s);
+    if (e != cudaSuccess) return cuda_fail(e, "clique: long roots");
+    return GZ_OK;
+}
+
 template <int K>
 gz_status launch_k(const GzView& v, int64_t n, int64_t lo, int64_t hi, cudaStream_t s,
                    unsigned long long* d_count, unsigned long long* d_work) {
@@ -419,77 +646,48 @@ gz_status launch_k(const GzView& v, int64_t n, int64_t lo, int64_t hi, cudaStrea
     GzView& mv = const_cast<GzView&>(v);
     gz_status st = gather_heavy(mv, n, s);
     if (st != GZ_OK) return st;
-    // heavy roots of [lo, hi) that fit the kernel, heaviest first, with the word
-    // offset of their prebuilt rows (16-byte aligned) and their parts
-    std::vector<std::pair<int32_t, int32_t>> hr;
+    st = build_heavy_rows(mv, mo, sms, s);
+    if (st != GZ_OK) return st;
+    // heavy roots of [lo, hi) with cached rows, heaviest first, each split into parts
+    std::vector<int> hi_idx;
     auto it = std::lower_bound(mv.heavy.begin(), mv.heavy.end(), std::make_pair((int32_t)lo, INT32_MIN));
-    for (; it != mv.heavy.end() && it->first < hi; ++it)
-        if (it->second <= mo) hr.push_back(*it);
-    std::stable_sort(hr.begin(), hr.end(), [](const std::pair<int32_t, int32_t>& a,
-                                              const std::pair<int32_t, int32_t>& b) {
-        return a.second > b.second;
+    for (; it != mv.heavy.end() && it->first < hi; ++it) {
+        const size_t i = (size_t)(it - mv.heavy.begin());
+        if (mv.heavy_rows && mv.heavy_off[i] != UINT32_MAX) hi_idx.push_back((int)i);
+    }
+    std::stable_sort(hi_idx.begin(), hi_idx.end(), [&](int a, int b) {
+        return mv.heavy[a].second > mv.heavy[b].second;
     });
-    std::vector<int4> roots_rows;
     std::vector<int4> ent;
-    uint64_t words = 0;
-    for (const auto& x : hr) {
-        const uint64_t sz = (uint64_t)x.second * (((x.second + 31) / 32) | 1);
-        if (words + sz > kHeavyRowWords) break;  // the rest run unsplit, rows built in place
-        roots_rows.push_back(make_int4(x.first, 0, (int)words, 0));
-        const int parts = parts_for(K, x.second);
-        for (int p = 0; p < parts; ++p) ent.push_back(make_int4(x.first, p | (parts << 16), (int)words, 0));
-        words += (sz + 3) & ~3ull;
+    for (int i : hi_idx) {
+        const int parts = parts_for(K, mv.heavy[i].second);
+        for (int p = 0; p < parts; ++p)
+            ent.push_back(make_int4(mv.heavy[i].first, p | (parts << 16), (int)mv.heavy_off[i], 0));
     }
-    // heavy roots beyond the row budget are not in the list: the chunk slots
-    // must not skip them, so the split threshold becomes their out-degree + 1
-    int heavy_d = kHeavyD;
-    if (roots_rows.size() < hr.size()) heavy_d = mo + 1;
-    if (heavy_d > mo) {
-        roots_rows.clear();
-        ent.clear();
-        words = 0;
-    }
+    // without cached rows no root is split (the chunk slots then take them all)
+    const int heavy_d = mv.heavy_rows ? kHeavyD : mo + 1;
     const size_t smem = ((size_t)mo * (((mo + 31) / 32) | 1) + 2 * (size_t)mo + 1) * 4;
-    const size_t smem_rows = ((size_t)mo * (((mo + 31) / 32) | 1) + mo) * 4;
     int4* d_ent = nullptr;
-    int4* d_hr = nullptr;
-    uint32_t* grows = nullptr;
     cudaError_t e = cudaSuccess;
     if (!ent.empty()) {
-        e = cudaMallocAsync(&d_ent, sizeof(int4) * (ent.size() + roots_rows.size()), s);
-        if (e == cudaSuccess) e = cudaMallocAsync(&grows, sizeof(uint32_t) * words, s);
-        if (e != cudaSuccess) {
-            if (d_ent) cudaFreeAsync(d_ent, s);
-            return cuda_fail(e, "clique: heavy rows");
-        }
-        d_hr = d_ent + ent.size();
-        e = cudaMemcpyAsync(d_ent, ent.data(), sizeof(int4) * ent.size(), cudaMemcpyHostToDevice, s);
+        e = cudaMallocAsync(&d_ent, sizeof(int4) * ent.size(), s);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(d_hr, roots_rows.data(), sizeof(int4) * roots_rows.size(),
-                                cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) {
-            cudaFuncSetAttribute(k_clique_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows);
-            int rb = sms * 2;
-            if ((int64_t)roots_rows.size() < rb) rb = (int)roots_rows.size();
-            k_clique_rows<<<rb, kThreads, smem_rows, s>>>(v.dag_rp, v.dag_col, d_hr,
-                                                         (int)roots_rows.size(), mo, grows);
-            GZ_COUNT_LAUNCH();
-        }
+            e = cudaMemcpyAsync(d_ent, ent.data(), sizeof(int4) * ent.size(), cudaMemcpyHostToDevice, s);
     }
     if (e == cudaSuccess) {
         cudaFuncSetAttribute(k_clique_big<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clique_big<K>, kThreads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clique_big<K>, kBigThreads, smem);
         int bb = sms * (per_sm > 0 ? per_sm : 1);
         const int64_t slots = (int64_t)ent.size() + (nroots + kBigPop - 1) / kBigPop;
         if (slots < bb) bb = (int)std::max<int64_t>(1, slots);
-        k_clique_big<K><<<bb, kThreads, smem, s>>>(v.dag_rp, v.dag_col, lo, hi, mo, heavy_d, d_ent,
-                                                    (int)ent.size(), grows, d_work + 1, d_count);
+        k_clique_big<K><<<bb, kBigThreads, smem, s>>>(v.dag_rp, v.dag_col, lo, hi, mo, heavy_d, d_ent,
+                                                       (int)ent.size(), mv.heavy_rows, d_work + 1, d_count);
         GZ_COUNT_LAUNCH();
+        e = cudaGetLastError();
     }
     if (d_ent) cudaFreeAsync(d_ent, s);
-    if (grows) cudaFreeAsync(grows, s);
-    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "clique launch");
+    if (v.max_out > kCliqueMaxOut) return launch_long<K>(mv, lo, hi, s, d_count, d_work + 2);
     return GZ_OK;
 }
 
@@ -507,8 +705,8 @@ bool clique_eligible(const GzProg& p, const gz_plan& plan, const GzView& v) {
 }
 
 // Adds the cliques of the roots in [lo, hi) whose out-list holds at most
-// kCliqueMaxOut vertices to *d_count; longer roots are left to the caller.
-// d_work holds two zeroed counters.
+// kCliqueLongOut vertices to *d_count; longer roots are left to the caller.
+// d_work holds three zeroed counters.
 gz_status clique_launch(int k, const GzView& v, int64_t n, int64_t lo, int64_t hi, cudaStream_t s,
                         unsigned long long* d_count, unsigned long long* d_work) {
     if (hi <= lo) return GZ_OK;

@@ -570,6 +570,10 @@ gz_status orient(gz_graph* g, cudaStream_t s) {
             o.has_dag = false;
             o.heavy.clear();
             o.heavy_built = false;
+            cudaFree(o.heavy_rows);
+            o.heavy_rows = nullptr;
+            o.heavy_off.clear();
+            o.heavy_rows_built = false;
         }
         if (o.src) { cudaFree(o.src); o.src = nullptr; }
         st = build_dag(g, &o, s);

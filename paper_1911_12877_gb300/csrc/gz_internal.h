@@ -85,6 +85,12 @@ struct GzView {
     // over several CTAs: (root, out-degree) pairs, gathered once per DAG build
     std::vector<std::pair<int32_t, int32_t>> heavy;
     bool heavy_built = false;
+    // bitset rows of those roots (out-degree <= kCliqueMaxOut), built once and
+    // kept for every later clique count of this view: heavy_off[i] is the word
+    // offset of heavy[i]'s rows in heavy_rows (UINT32_MAX: none)
+    uint32_t* heavy_rows = nullptr;
+    std::vector<uint32_t> heavy_off;
+    bool heavy_rows_built = false;
 };
 
 struct gz_graph {
@@ -138,12 +144,13 @@ gz_status count_one_in_region(const Query& Q, const LaunchCfg& cfg, cudaStream_t
                               uint64_t scratch_bytes, uint64_t* out_count);
 
 // clique side (gz_clique.cu): oriented k-cliques as bitsets over the root's out-list
-constexpr int kCliqueMaxOut = 1024;  // largest out-list kept in shared memory
+constexpr int kCliqueMaxOut = 1024;   // largest out-list whose rows fit in shared memory
+constexpr int kCliqueLongOut = 8192;  // largest out-list of the clique kernels (rows in global)
 bool clique_eligible(const GzProg& p, const gz_plan& plan, const GzView& v);
 // Enqueues nq queries on stream s: oriented cliques on the bitset kernels (their
 // roots with out-lists longer than kCliqueMaxOut on the general kernel), the rest
 // in one persistent general launch. Query i adds its count to d_counts[i];
-// d_work holds 2 zeroed counters per query; scratch as for count_launch.
+// d_work holds 3 zeroed counters per query; scratch as for count_launch.
 gz_status launch_mixed(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream_t s,
                        unsigned long long* d_counts, int* d_status, unsigned long long* d_work,
                        void* scratch, uint64_t scratch_bytes);

@@ -98,8 +98,8 @@ gz_status launch_batch(gz_server* s, Slot& sl) {
         if (st != GZ_OK) return st;
     }
     const uint64_t need = mixed_scratch_bytes(qs.data(), nq, kCfg) + 256;
-    // counts [nq], status, clique work counters [2 nq]
-    const size_t words = (size_t)nq + 1 + 2 * (size_t)nq;
+    // counts [nq], status, clique work counters [3 nq]
+    const size_t words = (size_t)nq + 1 + 3 * (size_t)nq;
     void* scratch = nullptr;
     unsigned long long* d = nullptr;
     cudaError_t e = cudaMallocAsync(&scratch, need, sl.stream);
