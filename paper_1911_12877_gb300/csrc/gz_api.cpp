@@ -188,27 +188,90 @@ uint64_t mixed_scratch_bytes(const Query* qs, int nq, const LaunchCfg& cfg) {
     return (uint64_t)resident_warps(cfg) * words * sizeof(int32_t);
 }
 
+// A small pool of streams per device on which one batch's queries overlap.
+constexpr int kPool = 4;
+gz_status stream_pool(cudaStream_t** out) {
+    static std::mutex mu;
+    static std::map<int, std::vector<cudaStream_t>> pools;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto& p = pools[dev];
+    if (p.empty()) {
+        p.resize(kPool);
+        for (auto& st : p) {
+            cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+            if (e != cudaSuccess) {
+                p.clear();
+                return cuda_fail(e, "stream pool");
+            }
+        }
+    }
+    *out = p.data();
+    return GZ_OK;
+}
+
 gz_status launch_mixed(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream_t s,
                        unsigned long long* d_counts, int* d_status, unsigned long long* d_work,
                        void* scratch, uint64_t scratch_bytes) {
     std::vector<Query> gen;
+    std::vector<int> cliq;
     for (int i = 0; i < nq; ++i) {
         Query q = qs[i];
         q.out_slot = i;
         if (q.unit_hi <= q.unit_lo) continue;
         if (q.plan && clique_eligible(*q.prog, *q.plan, *q.view)) {
-            const int64_t lo = q.root_lo < 0 ? 0 : q.root_lo;
-            const int64_t hi = (q.root_hi < 0 || q.root_hi > q.g->n) ? q.g->n : q.root_hi;
-            gz_status st = clique_launch(q.plan->k, *q.view, q.g->n, lo, hi, s, d_counts + i,
-                                         d_work + 3 * i);
+            gz_status st = clique_prepare(*q.view, q.g->n, s);
             if (st != GZ_OK) return st;
+            cliq.push_back(i);
             if (q.view->max_out <= kCliqueLongOut) continue;
             q.min_root_out = kCliqueLongOut + 1;  // roots the bitset kernels leave out
         }
         gen.push_back(q);
     }
-    if (gen.empty()) return GZ_OK;
-    return count_launch(gen.data(), (int)gen.size(), cfg, s, d_counts, scratch, scratch_bytes, d_status);
+    // one query (or one kind) runs on s; a mix of several forks onto the pool so
+    // the general kernel and the clique launches overlap on the device
+    const int kinds = (int)cliq.size() + (gen.empty() ? 0 : 1);
+    cudaStream_t* pool = nullptr;
+    if (kinds > 1 && stream_pool(&pool) != GZ_OK) pool = nullptr;
+    std::vector<cudaEvent_t> evs;
+    auto fork = [&](int j) -> cudaStream_t {
+        if (!pool) return s;
+        cudaStream_t t = pool[j % kPool];
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return s;
+        cudaEventRecord(ev, s);
+        cudaStreamWaitEvent(t, ev, 0);
+        evs.push_back(ev);
+        return t;
+    };
+    std::vector<cudaStream_t> used;
+    gz_status st = GZ_OK;
+    if (!gen.empty()) {
+        cudaStream_t t = fork(0);
+        used.push_back(t);
+        st = count_launch(gen.data(), (int)gen.size(), cfg, t, d_counts, scratch, scratch_bytes, d_status);
+    }
+    for (size_t c = 0; c < cliq.size() && st == GZ_OK; ++c) {
+        const Query& q = qs[cliq[c]];
+        const int64_t lo = q.root_lo < 0 ? 0 : q.root_lo;
+        const int64_t hi = (q.root_hi < 0 || q.root_hi > q.g->n) ? q.g->n : q.root_hi;
+        cudaStream_t t = fork((int)c + 1);
+        used.push_back(t);
+        st = clique_launch(q.plan->k, *q.view, q.g->n, lo, hi, t, d_counts + cliq[c], d_work + 3 * cliq[c]);
+    }
+    // join: s waits for every stream used
+    for (cudaStream_t t : used) {
+        if (t == s) continue;
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+            cudaEventRecord(ev, t);
+            cudaStreamWaitEvent(s, ev, 0);
+            evs.push_back(ev);
+        }
+    }
+    for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
+    return st;
 }
 
 // Runs nq queries (one launch_mixed) and copies their counts to the host.

@@ -56,39 +56,47 @@ __device__ __forceinline__ int index_of(const int32_t* O, int n, int32_t x) {
     return (lo < n && O[lo] == x) ? lo : -1;
 }
 
-// Sum over the cliques that extend the set AND(rs[0..nr)) (bits < lim) by
+// Sum over the cliques that extend the set AND(rs[0..NR)) (bits < lim) by
 // DEPTH more vertices, each below the previous one; DEPTH == 1 is a popcount.
-template <int DEPTH>
-__device__ unsigned long long extend(const uint32_t* rows, int W, const uint32_t** rs, int nr, int lim) {
+// NR is a template parameter so the row pointers stay in registers and the
+// AND over them unrolls; the popcount loop sums in 32 bits (at most lim).
+template <int DEPTH, int NR>
+__device__ __forceinline__ unsigned long long extend(const uint32_t* rows, int W,
+                                                     const uint32_t* const* rs, int lim) {
     const int words = (lim + 31) >> 5;
-    unsigned long long cnt = 0;
     if constexpr (DEPTH == 1) {
+        uint32_t cnt = 0;
         for (int w = 0; w < words; ++w) {
             uint32_t s = rs[0][w];
-            for (int i = 1; i < nr; ++i) s &= rs[i][w];
+#pragma unroll
+            for (int i = 1; i < NR; ++i) s &= rs[i][w];
             cnt += __popc(s);
         }
+        return cnt;
     } else {
+        unsigned long long cnt = 0;
+        const uint32_t* rn[NR + 1];
+#pragma unroll
+        for (int i = 0; i < NR; ++i) rn[i] = rs[i];
         for (int w = 0; w < words; ++w) {
             uint32_t s = rs[0][w];
-            for (int i = 1; i < nr; ++i) s &= rs[i][w];
+#pragma unroll
+            for (int i = 1; i < NR; ++i) s &= rs[i][w];
             while (s) {
                 const int c = (w << 5) + __ffs(s) - 1;
                 s &= s - 1;
-                rs[nr] = rows + (size_t)c * W;
-                cnt += extend<DEPTH - 1>(rows, W, rs, nr + 1, c);
+                rn[NR] = rows + (size_t)c * W;
+                cnt += extend<DEPTH - 1, NR + 1>(rows, W, rn, c);
             }
         }
+        return cnt;
     }
-    return cnt;
 }
 
 template <int K>
 __device__ __forceinline__ unsigned long long count_pair(const uint32_t* rows, int W, int a, int b) {
-    const uint32_t* rs[K];
-    rs[0] = rows + (size_t)a * W;
-    rs[1] = rows + (size_t)b * W;
-    return extend<K - 3>(rows, W, rs, 2, b);
+    const uint32_t* rs[2] = {rows + (size_t)a * W, rows + (size_t)b * W};
+    return extend<K - 3, 2>(rows, W, rs, b);
 }
 
 __device__ __forceinline__ unsigned long long block_sum(unsigned long long v, unsigned long long* red) {
@@ -555,6 +563,8 @@ gz_status build_heavy_rows(GzView& v, int mo, int sms, cudaStream_t s) {
         e = cudaGetLastError();
     }
     if (d_list) cudaFreeAsync(d_list, s);
+    // the rows are complete before any stream (other batch slots included) uses them
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         cudaFree(v.heavy_rows);
         v.heavy_rows = nullptr;
@@ -702,6 +712,20 @@ bool clique_eligible(const GzProg& p, const gz_plan& plan, const GzView& v) {
         if (plan.bp[i] != i - 1) return false;
     (void)p;
     return true;
+}
+
+// Builds the per-view state the clique kernels share between calls (the heavy
+// root list and their cached rows) on stream s, synchronously, so that later
+// launches on any stream may use it.
+gz_status clique_prepare(const GzView& v, int64_t n, cudaStream_t s) {
+    if (!v.has_dag || v.max_out <= 32) return GZ_OK;
+    GzView& mv = const_cast<GzView&>(v);
+    gz_status st = gather_heavy(mv, n, s);
+    if (st != GZ_OK) return st;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return build_heavy_rows(mv, (int)std::min<int64_t>(v.max_out, kCliqueMaxOut), sms, s);
 }
 
 // Adds the cliques of the roots in [lo, hi) whose out-list holds at most

@@ -50,7 +50,38 @@ struct KQ {
     int32_t out_slot;      // count slot of this query
     int64_t buf_off[GZ_MAXBUF];
     int64_t buf_cap[GZ_MAXBUF];
+    int64_t hash_off;      // per-warp hash table for a fixed operand too long for shared memory
+    int32_t hash_log2;     // its slot count is 1 << hash_log2 (0: none)
 };
+
+constexpr int kGlobalHashLog2 = 17;  // largest per-warp hash table in scratch (slots)
+
+// Per-warp scratch layout of a query: one buffer per compiled set operation
+// (max out-degree or max degree ids) and, when the last loop is flattened with
+// a fixed left operand that can outgrow the shared-memory hash set, a hash
+// table of up to 2^kGlobalHashLog2 slots. Returns the words per warp.
+uint64_t scratch_layout(const GzProg& p, const gz_graph& g, const GzView& v, KQ* k) {
+    uint64_t off = 0, capmax = 0;
+    for (int b = 0; b < p.nbuf; ++b) {
+        const uint64_t cap = (uint64_t)(p.buf_dag[b] ? v.max_out : g.max_deg);
+        if (k) {
+            k->buf_off[b] = (int64_t)off;
+            k->buf_cap[b] = (int64_t)cap;
+        }
+        off += (cap + 31) & ~31ull;
+    }
+    capmax = (uint64_t)g.max_deg;
+    int lg = 0;
+    if (p.flat == 1 && capmax > (uint64_t)kStageWords) {
+        while ((1ull << lg) < 2 * capmax && lg < kGlobalHashLog2) ++lg;
+    }
+    if (k) {
+        k->hash_off = (int64_t)off;
+        k->hash_log2 = lg;
+    }
+    if (lg) off += 1ull << lg;
+    return off;
+}
 
 // Number of elements of sorted L[0, n) that are < beta (warp-cooperative
 // 32-ary search; every lane returns the same value).
@@ -259,6 +290,31 @@ __device__ __forceinline__ void hash_build(int32_t* H, const int32_t* F, int64_t
     __syncwarp();
 }
 
+// The same open-addressing scheme in the warp's global scratch, 2^lg slots
+// (at least twice the keys), for fixed operands longer than kStageWords.
+__device__ __forceinline__ void ghash_build(int32_t* H, int lg, const int32_t* F, int64_t nF, int lane) {
+    const uint32_t mask = (1u << lg) - 1u;
+    for (int64_t i = lane; i <= (int64_t)mask; i += 32) H[i] = -1;
+    __syncwarp();
+    for (int64_t i = lane; i < nF; i += 32) {
+        const int32_t x = F[i];
+        uint32_t s = ((uint32_t)x * 0x9E3779B1u) >> (32 - lg);
+        while (atomicCAS(&H[s], -1, x) != -1) s = (s + 1) & mask;
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ bool ghash_has(const int32_t* H, int lg, int32_t x) {
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t s = ((uint32_t)x * 0x9E3779B1u) >> (32 - lg);
+    for (;;) {
+        const int32_t v = H[s];
+        if (v == x) return true;
+        if (v < 0) return false;
+        s = (s + 1) & mask;
+    }
+}
+
 __device__ __forceinline__ bool hash_has(const int32_t* H, int32_t x) {
     uint32_t s = hash_slot(x);
     for (;;) {
@@ -291,6 +347,8 @@ __device__ void last_level_flat(const KQ& q, const GzOp& op, WarpState& ws, List
     int64_t nF = 0;
     int32_t* H = sm + kStageWords + 128;
     bool hashed = false;
+    int32_t* GH = nullptr;  // global hash table (F too long for H), else NULL
+    int glg = 0;
     const bool sub = !shape2 && op.right_sub[0] != 0;
     const bool bounded = op.bound_pos >= 0;
     if (!shape2) {
@@ -312,6 +370,16 @@ __device__ void last_level_flat(const KQ& q, const GzOp& op, WarpState& ws, List
                 hash_build(H, F, nF, lane);
                 hashed = true;
             }
+        } else if (q.hash_log2 && S.n >= 16 && S.n * 64 >= nF && (2 * nF) <= (1ll << q.hash_log2)) {
+            // too long for shared memory: a hash table in the warp's scratch,
+            // sized to the next power of two >= 2 nF, when enough candidates
+            // probe it to pay for filling it
+            int lg = 1;
+            while ((1ll << lg) < 2 * nF) ++lg;
+            GH = scratch + q.hash_off;
+            glg = lg;
+            ghash_build(GH, lg, F, nF, lane);
+            hashed = true;
         }
     }
     const int sdag = shape2 ? op.left_dag : op.right_dag[0];
@@ -350,8 +418,9 @@ __device__ void last_level_flat(const KQ& q, const GzOp& op, WarpState& ws, List
         }
         // A streams N(c) and probes F (a hash lookup when F is hashed); B streams
         // F and binary-searches N(c) in global memory, several dependent loads
-        // per element, so with a hashed F A is taken up to 8x the length of B
-        const bool dirA = valid && (shape2 || m <= (hashed ? 8 * Lc : Lc));
+        // per element, so A is taken up to 8x (shared-memory hash) or 2x (hash
+        // in global scratch) the length of B
+        const bool dirA = valid && (shape2 || m <= (!hashed ? Lc : (GH ? 2 * Lc : 8 * Lc)));
         const bool dirB = valid && !dirA;
         for (int pass = 0; pass < 2; ++pass) {
             const bool mine = pass == 0 ? dirA : dirB;
@@ -389,7 +458,7 @@ __device__ void last_level_flat(const KQ& q, const GzOp& op, WarpState& ws, List
                         if (keep && !excluded(xm, ws, x)) acc += 1ull;
                         continue;
                     }
-                    found = hashed ? hash_has(H, x) : in_sorted(F, nF, x);
+                    found = !hashed ? in_sorted(F, nF, x) : (GH ? ghash_has(GH, glg, x) : hash_has(H, x));
                 } else {
                     x = F[i];
                     found = contains(rptr[lo], lens[lo], x);
@@ -553,14 +622,7 @@ void fill_kq(const Query& Q, KQ& k, uint64_t* words_out) {
     k.unit_count = Q.unit_hi - Q.unit_lo;
     k.min_root_out = Q.min_root_out;
     k.out_slot = 0;
-    uint64_t off = 0;
-    for (int b = 0; b < Q.prog->nbuf; ++b) {
-        uint64_t cap = (uint64_t)(Q.prog->buf_dag[b] ? v.max_out : Q.g->max_deg);
-        k.buf_off[b] = (int64_t)off;
-        k.buf_cap[b] = (int64_t)cap;
-        off += (cap + 31) & ~31ull;
-    }
-    *words_out = off;
+    *words_out = scratch_layout(*Q.prog, *Q.g, v, &k);
 }
 
 }  // namespace
@@ -623,12 +685,7 @@ gz_status count_one_in_region(const Query& Q, const LaunchCfg& cfg, cudaStream_t
 }
 
 uint64_t scratch_words_per_warp(const GzProg& p, const gz_graph& g, const GzView& v) {
-    uint64_t w = 0;
-    for (int b = 0; b < p.nbuf; ++b) {
-        uint64_t cap = (uint64_t)(p.buf_dag[b] ? v.max_out : g.max_deg);
-        w += (cap + 31) & ~31ull;
-    }
-    return w;
+    return scratch_layout(p, g, v, nullptr);
 }
 
 int resident_warps(const LaunchCfg& cfg) {
@@ -673,13 +730,7 @@ gz_status count_launch(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream
         k.min_root_out = Q.min_root_out;
         k.out_slot = Q.out_slot >= 0 ? Q.out_slot : i;
         total += k.unit_count;
-        uint64_t off = 0;
-        for (int b = 0; b < Q.prog->nbuf; ++b) {
-            uint64_t cap = (uint64_t)(Q.prog->buf_dag[b] ? v.max_out : Q.g->max_deg);
-            k.buf_off[b] = (int64_t)off;
-            k.buf_cap[b] = (int64_t)cap;
-            off += (cap + 31) & ~31ull;
-        }
+        const uint64_t off = scratch_layout(*Q.prog, *Q.g, v, &k);
         if (off > words) words = off;
     }
     if (total == 0) return GZ_OK;

@@ -156,6 +156,7 @@ gz_status launch_mixed(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream
                        void* scratch, uint64_t scratch_bytes);
 // Scratch bytes launch_mixed needs for these queries.
 uint64_t mixed_scratch_bytes(const Query* qs, int nq, const LaunchCfg& cfg);
+gz_status clique_prepare(const GzView& v, int64_t n, cudaStream_t s);
 gz_status clique_launch(int k, const GzView& v, int64_t n, int64_t lo, int64_t hi, cudaStream_t s,
                         unsigned long long* d_count, unsigned long long* d_work);
 

@@ -79,7 +79,7 @@ def adjacency(name_or_edges, k: int | None = None) -> np.ndarray:
 #: vertices; chordal cycles and K6 have counts of 10^12 and more on the
 #: skewed graphs above these scales, each costing seconds to minutes alone.
 BATCH_MAX_SCALE = {"wedge": 14, "path4": 14, "star3": 14, "c4": 14, "paw": 14, "chordal6": 13,
-                   "chordal5": 15, "k6": 16, "diamond": 18, "k5": 18, "triangle": 21, "k4": 21}
+                   "chordal5": 15, "k6": 16, "diamond": 16, "k5": 18, "triangle": 21, "k4": 21}
 
 
 def batch_queries(scales=None, per_graph: int = 4, seed: int = 4):
