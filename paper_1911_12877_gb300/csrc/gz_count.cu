@@ -28,8 +28,11 @@ namespace gz {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kStageWords = 1024;  // per-warp shared staging of a fixed operand (int32)
-constexpr int kHashSlots = 2048;   // per-warp open-addressing hash set of that operand
+// Shared memory per warp stays small (6.6 KB): the rest of the SM's unified
+// L1/shared storage caches the neighbour lists the binary searches walk.
+constexpr int kStageWords = 512;   // per-warp shared staging of a fixed operand (int32)
+constexpr int kHashLog2 = 10;
+constexpr int kHashSlots = 1 << kHashLog2;  // per-warp open-addressing hash set of that operand
 // per warp: staged operand, lane offsets, lengths, list pointers, hash set
 constexpr int kWarpSmemWords = kStageWords + 64 + 64 + kHashSlots;
 
@@ -276,7 +279,7 @@ __device__ __forceinline__ bool excluded(uint8_t mask, const WarpState& ws, int3
 // (kHashSlots slots, -1 = empty, linear probing). At most kStageWords keys, so
 // the load factor stays <= 1/2 and every probe ends at an empty slot.
 __device__ __forceinline__ uint32_t hash_slot(int32_t x) {
-    return ((uint32_t)x * 0x9E3779B1u) >> (32 - 11);
+    return ((uint32_t)x * 0x9E3779B1u) >> (32 - kHashLog2);
 }
 
 __device__ __forceinline__ void hash_build(int32_t* H, const int32_t* F, int64_t nF, int lane) {
