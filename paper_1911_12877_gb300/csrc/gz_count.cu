@@ -441,12 +441,9 @@ __device__ void last_level_flat(const KQ& q, const GzOp& op, WarpState& ws, List
             lens[lane] = (int32_t)m;
             rptr[lane] = R;
             __syncwarp();
+            int lo = 0;  // first lane whose inclusive offset exceeds f (monotone in f)
             for (int64_t f = lane; f < total; f += 32) {
-                int lo = 0, hi = 31;  // first lane whose inclusive offset exceeds f
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (offs[mid] > f) hi = mid; else lo = mid + 1;
-                }
+                while (offs[lo] <= f) ++lo;
                 const int64_t i = f - (lo ? offs[lo - 1] : 0);
                 bool found;
                 int32_t x;
