@@ -16,6 +16,7 @@
 //  - Counts are per-lane uint64, reduced by warp shuffles and added to the
 //    query's slot with one atomic per warp per query. Integer adds are exact and
 //    order-independent, so the result is bit-exact whatever the schedule.
+#include <algorithm>
 #include <climits>
 #include <cstdio>
 #include <cstring>
@@ -85,6 +86,26 @@ uint64_t scratch_layout(const GzProg& p, const gz_graph& g, const GzView& v, KQ*
     if (lg) off += 1ull << lg;
     return off;
 }
+
+// Splitting of heavy units. A unit whose loop-2 candidate list holds at least
+// kSplitMin vertices is not run by the warp that popped it: the first pass
+// records it (launch-space unit index and candidate count), a one-CTA scan
+// turns the records into chunks of kSplitChunk candidates, and a second pass
+// hands the chunks to warps, each recomputing loop 1 and walking its chunk of
+// loop 2. A hub edge then spreads over many warps instead of holding one.
+constexpr int64_t kSplitMin = 512;
+constexpr int64_t kSplitChunk = 256;
+
+struct Deferred {
+    int64_t unit;  // launch-space unit index
+    int64_t n2;    // loop-2 candidates
+};
+
+struct DeferCtl {
+    Deferred* list;              // NULL: no deferral
+    unsigned long long* count;   // records written (may exceed cap)
+    int64_t cap;
+};
 
 // Number of elements of sorted L[0, n) that are < beta (warp-cooperative
 // 32-ary search; every lane returns the same value).
@@ -337,7 +358,7 @@ __device__ __forceinline__ bool hash_has(const int32_t* H, int32_t x) {
 // the fixed right lists; (B) F[<b_c], binary-searching N(c)[<b_c]. Both passes
 // are flattened, so lanes stream the concatenated lists of many candidates and
 // no lane idles on a short list.
-__device__ void last_level_flat(const KQ& q, const GzOp& op, WarpState& ws, ListRef S,
+__device__ void last_level_flat(const KQ& q, const GzOp& op, WarpState& ws, ListRef S, int64_t ioff,
                                 int32_t* scratch, int32_t* sm, int lane, unsigned long long& acc) {
     const GzProg& P = q.prog;
     const int t = P.k - 2;
@@ -406,7 +427,7 @@ __device__ void last_level_flat(const KQ& q, const GzOp& op, WarpState& ws, List
             if (bounded) beta = op.bound_pos == t ? c : ws.emb[op.bound_pos];
             if (bounded && sdag != 2) m = lane_lower_bound(R, m, beta);
             if (!shape2) {
-                if (bounded && op.bound_pos == t) Lc = op.left_iter ? idx : lane_lower_bound(F, nF, c);
+                if (bounded && op.bound_pos == t) Lc = op.left_iter ? idx + ioff : lane_lower_bound(F, nF, c);
                 else Lc = nF;
                 if (Lc == 0) valid = false;  // empty left part: contributes nothing
             }
@@ -472,8 +493,13 @@ __device__ void last_level_flat(const KQ& q, const GzOp& op, WarpState& ws, List
     __syncwarp();
 }
 
+// Runs one unit (e0, e1), loop 2 restricted to candidates [lo2, hi2) (hi2 < 0:
+// all). With df.list set, a unit with at least kSplitMin loop-2 candidates is
+// recorded for the split pass instead (u = its launch-space index).
 __device__ void process_unit(const KQ& q, int64_t unit, WarpState& ws, int32_t* scratch,
-                             int32_t* sm, int lane, unsigned long long& acc, int* status) {
+                             int32_t* sm, int lane, unsigned long long& acc, int* status,
+                             int64_t lo2 = 0, int64_t hi2 = -1, const DeferCtl* df = nullptr,
+                             int64_t u = 0) {
     const GzProg& P = q.prog;
     const int k = P.k;
     const int32_t e0 = q.usrc[unit];
@@ -488,10 +514,23 @@ __device__ void process_unit(const KQ& q, int64_t unit, WarpState& ws, int32_t* 
     }
     run_level(q, 1, ws, scratch, lane, acc, status);
     if (k == 3) return;
+    const ListRef c2 = cand_list(q, 2, ws, scratch, lane);
+    if (df && df->list && c2.n >= kSplitMin) {
+        unsigned long long slot = 0;
+        if (lane == 0) slot = atomicAdd(df->count, 1ull);
+        slot = __shfl_sync(kFull, slot, 0);
+        if ((int64_t)slot < df->cap) {
+            if (lane == 0) df->list[slot] = Deferred{u, c2.n};
+            __syncwarp();
+            return;
+        }
+    }
+    if (hi2 < 0 || hi2 > c2.n) hi2 = c2.n;
+    if (lo2 >= hi2) return;
     const bool flat = P.flat != 0;
     if (k == 4 && flat) {
-        last_level_flat(q, P.ops[P.level_begin[2]], ws, cand_list(q, 2, ws, scratch, lane), scratch, sm,
-                        lane, acc);
+        ListRef S{c2.p + lo2, hi2 - lo2};
+        last_level_flat(q, P.ops[P.level_begin[2]], ws, S, lo2, scratch, sm, lane, acc);
         return;
     }
     // explicit DFS over loops 2..k-2 (2..k-3 when the last loop is flattened)
@@ -499,10 +538,7 @@ __device__ void process_unit(const KQ& q, int64_t unit, WarpState& ws, int32_t* 
     const int32_t* cp[GZ_MAX_K];
     int64_t cn[GZ_MAX_K], it[GZ_MAX_K];
     int d = 2;
-    {
-        ListRef r = cand_list(q, 2, ws, scratch, lane);
-        cp[2] = r.p; cn[2] = r.n; it[2] = 0;
-    }
+    cp[2] = c2.p; cn[2] = hi2; it[2] = lo2;
     while (d >= 2) {
         if (it[d] >= cn[d]) { --d; continue; }
         const int64_t pos = it[d]++;
@@ -521,7 +557,7 @@ __device__ void process_unit(const KQ& q, int64_t unit, WarpState& ws, int32_t* 
             ListRef r = cand_list(q, d, ws, scratch, lane);
             cp[d] = r.p; cn[d] = r.n; it[d] = 0;
         } else if (flat) {
-            last_level_flat(q, P.ops[P.level_begin[k - 2]], ws, cand_list(q, k - 2, ws, scratch, lane),
+            last_level_flat(q, P.ops[P.level_begin[k - 2]], ws, cand_list(q, k - 2, ws, scratch, lane), 0,
                             scratch, sm, lane, acc);
         }
     }
@@ -540,7 +576,7 @@ __global__ void __launch_bounds__(256, 2) k_enumerate(const KQ* __restrict__ qs,
                                                    unsigned long long* __restrict__ counts,
                                                    int* __restrict__ status,
                                                    int32_t* __restrict__ scratch,
-                                                   int64_t words_per_warp) {
+                                                   int64_t words_per_warp, DeferCtl df) {
     extern __shared__ int32_t smem[];
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -571,8 +607,95 @@ __global__ void __launch_bounds__(256, 2) k_enumerate(const KQ* __restrict__ qs,
                 cur = lo;
             }
             const KQ& q = qs[cur];
-            process_unit(q, q.unit_lo + (u - q.unit_begin), ws, my, sm, lane, acc, status);
+            process_unit(q, q.unit_lo + (u - q.unit_begin), ws, my, sm, lane, acc, status, 0, -1, &df, u);
         }
+    }
+    if (cur >= 0) {
+        unsigned long long s = warp_sum(acc);
+        if (lane == 0 && s) atomicAdd(&counts[qs[cur].out_slot], s);
+    }
+}
+
+// prefix[i] = chunks of the deferred records before record i (exclusive), for
+// the min(count, cap) records of the first pass; prefix[n] = all chunks. One CTA.
+__global__ void __launch_bounds__(1024) k_split_scan(const Deferred* __restrict__ dl,
+                                                     const unsigned long long* __restrict__ dcount,
+                                                     int64_t cap, int64_t* __restrict__ prefix) {
+    __shared__ int64_t part[1024];
+    const int64_t n = (int64_t)*dcount < cap ? (int64_t)*dcount : cap;
+    const int64_t per = (n + 1023) / 1024;
+    const int64_t b = threadIdx.x * per, e = b + per < n ? b + per : n;
+    int64_t sum = 0;
+    for (int64_t i = b; i < e; ++i) sum += (dl[i].n2 + kSplitChunk - 1) / kSplitChunk;
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t run = 0;
+        for (int i = 0; i < 1024; ++i) {
+            const int64_t x = part[i];
+            part[i] = run;
+            run += x;
+        }
+        prefix[n] = run;
+    }
+    __syncthreads();
+    int64_t run = part[threadIdx.x];
+    for (int64_t i = b; i < e; ++i) {
+        prefix[i] = run;
+        run += (dl[i].n2 + kSplitChunk - 1) / kSplitChunk;
+    }
+}
+
+// Second pass: chunk t of the deferred units, one per warp pop.
+__global__ void __launch_bounds__(256, 2) k_enumerate_split(const KQ* __restrict__ qs, int nq,
+                                                         const Deferred* __restrict__ dl,
+                                                         const unsigned long long* __restrict__ dcount,
+                                                         int64_t cap,
+                                                         const int64_t* __restrict__ prefix,
+                                                         unsigned long long* __restrict__ work,
+                                                         unsigned long long* __restrict__ counts,
+                                                         int* __restrict__ status,
+                                                         int32_t* __restrict__ scratch,
+                                                         int64_t words_per_warp) {
+    extern __shared__ int32_t smem[];
+    const int lane = threadIdx.x & 31;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int32_t* my = scratch + gwarp * words_per_warp;
+    int32_t* sm = smem + (threadIdx.x >> 5) * kWarpSmemWords;
+    const int64_t n = (int64_t)*dcount < cap ? (int64_t)*dcount : cap;
+    const int64_t total = prefix[n];
+    WarpState ws;
+    unsigned long long acc = 0;
+    int cur = -1;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(work, 1ull);
+        t = __shfl_sync(kFull, t, 0);
+        if ((int64_t)t >= total) break;
+        int64_t lo = 0, hi = n - 1;  // last record with prefix <= t
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= (int64_t)t) lo = mid; else hi = mid - 1;
+        }
+        const Deferred rec = dl[lo];
+        const int64_t c0 = ((int64_t)t - prefix[lo]) * kSplitChunk;
+        const int64_t u = rec.unit;
+        if (cur < 0 || u < qs[cur].unit_begin || u >= qs[cur].unit_begin + qs[cur].unit_count) {
+            if (cur >= 0) {
+                unsigned long long s = warp_sum(acc);
+                if (lane == 0 && s) atomicAdd(&counts[qs[cur].out_slot], s);
+                acc = 0;
+            }
+            int a = 0, b = nq - 1;
+            while (a < b) {
+                const int mid = (a + b + 1) >> 1;
+                if (qs[mid].unit_begin <= u) a = mid; else b = mid - 1;
+            }
+            cur = a;
+        }
+        const KQ& q = qs[cur];
+        process_unit(q, q.unit_lo + (u - q.unit_begin), ws, my, sm, lane, acc, status, c0,
+                     c0 + kSplitChunk);
     }
     if (cur >= 0) {
         unsigned long long s = warp_sum(acc);
@@ -740,22 +863,46 @@ gz_status count_launch(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream
                   (unsigned long long)((uint64_t)warps * words * 4));
         return GZ_ENOMEM;
     }
-    KQ* d = nullptr;
-    unsigned long long* work = nullptr;
-    cudaError_t e = cudaMallocAsync(&d, sizeof(KQ) * nq + 16, s);
+    // one allocation: queries | 4 counters (pass-1 queue, pass-2 queue, records) |
+    // deferred records [cap] | chunk prefix [cap + 1]
+    bool split = false;
+    for (int i = 0; i < nq; ++i) split = split || qs[i].prog->k >= 4;
+    const int64_t cap = split ? std::min<int64_t>(total, (int64_t)1 << 20) : 0;
+    const size_t qbytes = (sizeof(KQ) * nq + 255) & ~(size_t)255;
+    const size_t bytes = qbytes + 32 + sizeof(Deferred) * cap + sizeof(int64_t) * (cap + 1);
+    char* base = nullptr;
+    cudaError_t e = cudaMallocAsync(&base, bytes, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync queries");
-    work = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(d) + sizeof(KQ) * nq);
+    KQ* d = reinterpret_cast<KQ*>(base);
+    unsigned long long* work = reinterpret_cast<unsigned long long*>(base + qbytes);
+    Deferred* dl = reinterpret_cast<Deferred*>(base + qbytes + 32);
+    int64_t* prefix = reinterpret_cast<int64_t*>(dl + cap);
     e = cudaMemcpyAsync(d, h.data(), sizeof(KQ) * nq, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(work, 0, 16, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(work, 0, 32, s);
     if (e == cudaSuccess) {
         const int blocks = warps / cfg.block_warps;
+        DeferCtl df{split ? dl : nullptr, work + 2, cap};
         k_enumerate<<<blocks, cfg.block_warps * 32, cfg.block_warps * kWarpSmemWords * 4, s>>>(
             d, nq, total, cfg.chunk > 0 ? cfg.chunk : 1, work, d_counts, d_status,
-            reinterpret_cast<int32_t*>(scratch), (int64_t)words);
+            reinterpret_cast<int32_t*>(scratch), (int64_t)words, df);
         GZ_COUNT_LAUNCH();
+        if (split) {
+            k_split_scan<<<1, 1024, 0, s>>>(dl, work + 2, cap, prefix);
+            GZ_COUNT_LAUNCH();
+            static bool attr = false;
+            if (!attr) {
+                cudaFuncSetAttribute(k_enumerate_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     8 * kWarpSmemWords * 4);
+                attr = true;
+            }
+            k_enumerate_split<<<blocks, cfg.block_warps * 32, cfg.block_warps * kWarpSmemWords * 4, s>>>(
+                d, nq, dl, work + 2, cap, prefix, work + 1, d_counts, d_status,
+                reinterpret_cast<int32_t*>(scratch), (int64_t)words);
+            GZ_COUNT_LAUNCH();
+        }
         e = cudaGetLastError();
     }
-    cudaFreeAsync(d, s);
+    cudaFreeAsync(base, s);
     if (e != cudaSuccess) return cuda_fail(e, "enumerate launch");
     return GZ_OK;
 }

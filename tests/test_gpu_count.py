@@ -304,3 +304,23 @@ def test_cliques_with_out_lists_beyond_the_bitset_limit():
     assert gz.count(gz.Plan("k4"), G, orientation=True) == (m // 2) ** 2
     assert gz.count(gz.Plan("k5"), G, orientation=True) == 0
     assert gz.count(gz.Plan("k4"), G, orientation=True) == oracle_count("k4", g)
+
+
+@pytest.mark.parametrize("name", ["diamond", "paw", "c4", "house", "chordal5", "hourglass"])
+def test_split_units_book_graph(name):
+    """Units whose loop-2 candidate list reaches the split threshold (512) are
+    deferred, cut into chunks and finished by other warps; the count must not
+    change. Book graph: an edge (0, 1) whose ends share 700 neighbours, plus a
+    seeded sprinkling of edges among those neighbours."""
+    rng = np.random.default_rng(7)
+    pages = list(range(2, 702))
+    e = [(0, 1)] + [(0, p) for p in pages] + [(1, p) for p in pages]
+    extra = rng.choice(pages, size=(900, 2))
+    e += [(int(a), int(b)) for a, b in extra if a != b]
+    g = S.from_edges(702, e, "book700")
+    G = gz.Graph.from_csr(g).orient()
+    p = gz.Plan(name)
+    want = oracle_count(name, g)
+    assert gz.count(p, G, orientation=True) == want
+    assert gz.count(p, G, orientation=False) == want
+    assert gz.count_batch([p, p], [G, G], [True, False]) == [want, want]
