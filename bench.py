@@ -141,9 +141,9 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the clique kernels' source file (the kernels the roofline figures are for)."""
     h = hashlib.sha256()
-    for f in ("gz_clique.cu", "gz_internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_1911_12877_gb300", "csrc", f), "rb").read())
+    h.update(open(os.path.join(ROOT, "paper_1911_12877_gb300", "csrc", "gz_clique.cu"), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -576,7 +576,7 @@ def run_served(args, dist, world, rank, local):
         gidx = np.zeros(nreq, np.int32)
         rec = {}
         for mode in ("served", "fifo"):
-            srv = gz.Server(max_inflight=4, max_batch=64)
+            srv = gz.Server(max_inflight=args.inflight, max_batch=args.max_batch)
             counts, lat, st = srv.replay(plans, [G], [1] * nreq, arr, pidx, gidx, fifo=(mode == "fifo"))
             srv.close()
             if [int(c) for c in counts] != [alone[i] for i in pidx]:
@@ -616,6 +616,8 @@ def main(argv=None):
                     "(default none at scale 22, all below)")
     ap.add_argument("--requests", type=int, default=300, help="served config: requests per rate")
     ap.add_argument("--rates", default="12.5,25,50,100,200", help="served config: Poisson rates")
+    ap.add_argument("--inflight", type=int, default=4, help="served config: concurrent launches")
+    ap.add_argument("--max-batch", type=int, default=64, help="served config: requests per launch")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "gz":
         args.warmup = 3

@@ -213,7 +213,7 @@ gz_status stream_pool(cudaStream_t** out) {
 
 gz_status launch_mixed(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream_t s,
                        unsigned long long* d_counts, int* d_status, unsigned long long* d_work,
-                       void* scratch, uint64_t scratch_bytes) {
+                       void* scratch, uint64_t scratch_bytes, bool overlap) {
     std::vector<Query> gen;
     std::vector<int> cliq;
     for (int i = 0; i < nq; ++i) {
@@ -233,7 +233,7 @@ gz_status launch_mixed(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream
     // the general kernel and the clique launches overlap on the device
     const int kinds = (int)cliq.size() + (gen.empty() ? 0 : 1);
     cudaStream_t* pool = nullptr;
-    if (kinds > 1 && stream_pool(&pool) != GZ_OK) pool = nullptr;
+    if (overlap && kinds > 1 && stream_pool(&pool) != GZ_OK) pool = nullptr;
     std::vector<cudaEvent_t> evs;
     auto fork = [&](int j) -> cudaStream_t {
         if (!pool) return s;
@@ -293,7 +293,7 @@ gz_status run_queries(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream_
         cudaFreeAsync(d, s);
         return cuda_fail(e, "memset counts");
     }
-    st = launch_mixed(qs, nq, cfg, s, d, d_status, d + nq + 1, a.ptr, a.bytes);
+    st = launch_mixed(qs, nq, cfg, s, d, d_status, d + nq + 1, a.ptr, a.bytes, true);
     std::vector<unsigned long long> h(nq + 1);
     if (st == GZ_OK) {
         e = cudaMemcpyAsync(h.data(), d, sizeof(unsigned long long) * (nq + 1), cudaMemcpyDeviceToHost, s);

@@ -394,7 +394,7 @@ __device__ void last_level_flat(const KQ& q, const GzOp& op, WarpState& ws, List
                 hash_build(H, F, nF, lane);
                 hashed = true;
             }
-        } else if (q.hash_log2 && S.n >= 16 && S.n * 64 >= nF && (2 * nF) <= (1ll << q.hash_log2)) {
+        } else if (q.hash_log2 && S.n >= 16 && S.n * 4 >= nF && (2 * nF) <= (1ll << q.hash_log2)) {
             // too long for shared memory: a hash table in the warp's scratch,
             // sized to the next power of two >= 2 nF, when enough candidates
             // probe it to pay for filling it
@@ -412,6 +412,24 @@ __device__ void last_level_flat(const KQ& q, const GzOp& op, WarpState& ws, List
     // exclusion count below has to consider c.
     const uint8_t xm = op.excl_mask & (uint8_t)~(1u << t);
     const bool excl_self = (op.excl_mask >> t) & 1;
+    // Shape 2 whose right lists are all subtracted (at most two) under a bound
+    // that does not move with c: |L - R0 - R1| with L = N(c)[<b] is counted as
+    // |L| - |L & R0| - |L & R1| + |L & R0 & R1| (a set identity), each
+    // intersection streaming its shortest list and probing the others, instead
+    // of streaming L and probing both. A hub candidate then costs about the
+    // length of the fixed lists, not its own degree.
+    bool ie = shape2 && op.nright >= 1 && op.nright <= 2 && (!bounded || op.bound_pos != t);
+    for (int r = 0; r < op.nright && ie; ++r) ie = op.right_sub[r] != 0;
+    ListRef rl[2] = {{nullptr, 0}, {nullptr, 0}};
+    if (ie) {
+        const int32_t bfix = bounded ? ws.emb[op.bound_pos] : INT_MAX;
+        for (int r = 0; r < op.nright; ++r) {
+            rl[r] = adj_list(q, ws.emb[op.right_pos[r]], op.right_dag[r]);
+            if (bounded && op.right_dag[r] != 2) rl[r].n = warp_lower_bound(rl[r].p, rl[r].n, bfix, lane);
+        }
+    }
+    const int32_t** spt = reinterpret_cast<const int32_t**>(sm);  // shape 2 leaves F's staging free
+    int32_t* pmask = sm + 64;
     for (int64_t base = 0; base < S.n; base += 32) {
         const int64_t idx = base + lane;
         bool valid = idx < S.n;
@@ -431,6 +449,66 @@ __device__ void last_level_flat(const KQ& q, const GzOp& op, WarpState& ws, List
                 else Lc = nF;
                 if (Lc == 0) valid = false;  // empty left part: contributes nothing
             }
+        }
+        if (ie) {
+            if (valid) {
+                acc += (unsigned long long)m;
+                for (int j = 0; j < GZ_MAX_K; ++j)  // excluded vertices the identity would count
+                    if (xm >> j & 1) {
+                        const int32_t e = ws.emb[j];
+                        if (e < beta && in_sorted(R, m, e)) {
+                            bool keep = true;
+                            for (int r = 0; r < op.nright; ++r) keep = keep && !in_sorted(rl[r].p, rl[r].n, e);
+                            if (keep) acc -= 1ull;
+                        }
+                    }
+            }
+            const int nterms = op.nright == 2 ? 3 : 1;
+            for (int term = 0; term < nterms; ++term) {
+                const unsigned set = term == 0 ? 1u : (term == 1 ? 2u : 3u);  // which R_r
+                const bool plus = term == 2;
+                // stream the shortest of L and the set's lists; probe the others
+                // (mask bit 0: L = N(c)[<b], bits 1-2: R0, R1)
+                const int32_t* sp = R;
+                int64_t sl = m;
+                unsigned pm = set << 1;
+                for (int r = 0; r < 2; ++r)
+                    if ((set >> r & 1) && rl[r].n < sl) {
+                        sp = rl[r].p;
+                        sl = rl[r].n;
+                        pm = (set << 1 | 1u) & ~(2u << r);
+                    }
+                if (!valid) sl = 0;
+                if (!__any_sync(kFull, sl > 0)) continue;
+                int64_t incl = sl;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int64_t v = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                const int64_t total = __shfl_sync(kFull, incl, 31);
+                __syncwarp();
+                offs[lane] = (int32_t)incl;
+                lens[lane] = (int32_t)m;
+                rptr[lane] = R;
+                spt[lane] = sp;
+                pmask[lane] = (int32_t)pm;
+                __syncwarp();
+                int lo = 0;
+                for (int64_t f = lane; f < total; f += 32) {
+                    while (offs[lo] <= f) ++lo;
+                    const int64_t i = f - (lo ? offs[lo - 1] : 0);
+                    const int32_t x = __ldg(spt[lo] + i);
+                    const unsigned msk = (unsigned)pmask[lo];
+                    bool found = true;
+                    if (msk & 1u) found = contains(rptr[lo], lens[lo], x);
+                    if (found && (msk & 2u)) found = in_sorted(rl[0].p, rl[0].n, x);
+                    if (found && (msk & 4u)) found = in_sorted(rl[1].p, rl[1].n, x);
+                    if (found) acc += plus ? 1ull : ~0ull;
+                }
+                __syncwarp();
+            }
+            continue;
         }
         if (valid && sub) {
             acc += (unsigned long long)Lc;  // |F part|; matches are subtracted below

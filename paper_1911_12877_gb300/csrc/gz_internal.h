@@ -148,12 +148,14 @@ constexpr int kCliqueMaxOut = 1024;   // largest out-list whose rows fit in shar
 constexpr int kCliqueLongOut = 8192;  // largest out-list of the clique kernels (rows in global)
 bool clique_eligible(const GzProg& p, const gz_plan& plan, const GzView& v);
 // Enqueues nq queries on stream s: oriented cliques on the bitset kernels (their
-// roots with out-lists longer than kCliqueMaxOut on the general kernel), the rest
+// roots with out-lists longer than kCliqueLongOut on the general kernel), the rest
 // in one persistent general launch. Query i adds its count to d_counts[i];
-// d_work holds 3 zeroed counters per query; scratch as for count_launch.
+// d_work holds 3 zeroed counters per query; scratch as for count_launch. With
+// overlap, a mix of queries forks onto a per-device stream pool and joins s
+// again (the server passes false: its slots already overlap on their own streams).
 gz_status launch_mixed(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream_t s,
                        unsigned long long* d_counts, int* d_status, unsigned long long* d_work,
-                       void* scratch, uint64_t scratch_bytes);
+                       void* scratch, uint64_t scratch_bytes, bool overlap);
 // Scratch bytes launch_mixed needs for these queries.
 uint64_t mixed_scratch_bytes(const Query* qs, int nq, const LaunchCfg& cfg);
 gz_status clique_prepare(const GzView& v, int64_t n, cudaStream_t s);

@@ -109,7 +109,7 @@ gz_status launch_batch(gz_server* s, Slot& sl) {
     gz_status st = e == cudaSuccess ? GZ_OK : cuda_fail(e, "server: memset");
     if (st == GZ_OK)
         st = launch_mixed(qs.data(), nq, kCfg, sl.stream, d, reinterpret_cast<int*>(d + nq), d + nq + 1,
-                          scratch, need);
+                          scratch, need, false);
     if (st == GZ_OK) {
         e = cudaMemcpyAsync(sl.h_counts, d, sizeof(unsigned long long) * (nq + 1), cudaMemcpyDeviceToHost, sl.stream);
         if (e != cudaSuccess) st = cuda_fail(e, "server: copy back");

@@ -324,3 +324,26 @@ def test_split_units_book_graph(name):
     assert gz.count(p, G, orientation=True) == want
     assert gz.count(p, G, orientation=False) == want
     assert gz.count_batch([p, p], [G, G], [True, False]) == [want, want]
+
+
+def test_server_wait_statuses():
+    """gz_server_wait: a wait that runs out returns GZ_ETIMEOUT and leaves the
+    request pending; a later wait gets its count; an unknown (or already
+    collected) ticket is GZ_EINVAL."""
+    g = S.rmat(14, 16, 51)
+    G = gz.Graph.from_csr(g).orient()
+    p = gz.Plan("chordal5")
+    want = gz.count(p, G, True)
+    srv = gz.Server(max_inflight=1, max_batch=4)
+    t = srv.submit(p, G, True)
+    with pytest.raises(gz.GzError) as e:
+        srv.wait(t, timeout_ms=0)
+    assert e.value.status == gz.GZ_ETIMEOUT
+    assert srv.wait(t)[0] == want
+    with pytest.raises(gz.GzError) as e:
+        srv.wait(t, timeout_ms=0)
+    assert e.value.status == gz.GZ_EINVAL
+    with pytest.raises(gz.GzError) as e:
+        srv.wait(987654, timeout_ms=0)
+    assert e.value.status == gz.GZ_EINVAL
+    srv.close()
