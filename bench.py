@@ -616,8 +616,8 @@ def main(argv=None):
                     "(default none at scale 22, all below)")
     ap.add_argument("--requests", type=int, default=300, help="served config: requests per rate")
     ap.add_argument("--rates", default="12.5,25,50,100,200", help="served config: Poisson rates")
-    ap.add_argument("--inflight", type=int, default=4, help="served config: concurrent launches")
-    ap.add_argument("--max-batch", type=int, default=64, help="served config: requests per launch")
+    ap.add_argument("--inflight", type=int, default=2, help="served config: concurrent launches")
+    ap.add_argument("--max-batch", type=int, default=8, help="served config: requests per launch")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "gz":
         args.warmup = 3

@@ -394,7 +394,7 @@ __device__ void last_level_flat(const KQ& q, const GzOp& op, WarpState& ws, List
                 hash_build(H, F, nF, lane);
                 hashed = true;
             }
-        } else if (q.hash_log2 && S.n >= 16 && S.n * 4 >= nF && (2 * nF) <= (1ll << q.hash_log2)) {
+        } else if (q.hash_log2 && S.n >= 16 && S.n * 64 >= nF && (2 * nF) <= (1ll << q.hash_log2)) {
             // too long for shared memory: a hash table in the warp's scratch,
             // sized to the next power of two >= 2 nF, when enough candidates
             // probe it to pay for filling it
