@@ -164,6 +164,13 @@ void gz_plan_destroy(gz_plan* p);
  * original ids (use_orientation = 0) or the reindexed graph (1; requires
  * gz_orient first). The graph stays on the device; *out_count (host) receives
  * the exact count. Scratch is allocated by the library and reused.
+ *
+ * Oriented k-cliques (4 <= k <= 8) run on the bitset clique kernels: the rows of
+ * roots with at least 128 out-neighbours are built once per out-list view and
+ * kept on the device until the view is rebuilt (gz_orient) or the graph is
+ * destroyed; roots with more than 8192 out-neighbours go to the general kernel
+ * in the same call. Every other plan runs on the general kernel, whose first
+ * pass hands edges with many loop-2 candidates to a second, split pass.
  * Errors: GZ_EINVAL, GZ_ENOMEM, GZ_ECUDA.
  */
 gz_status gz_count(const gz_plan* p, const gz_graph* g, int use_orientation, void* stream,
@@ -220,10 +227,12 @@ gz_status gz_scratch_bytes(const gz_plan* p, const gz_graph* g, int use_orientat
 
 /*
  * Batched counting: nq independent (plan, graph, use_orientation[i]) queries in
- * one persistent launch over a device work queue (no paper counterpart; the
- * merged multi-pattern program of Sec. 3 is the closest). out_counts[nq] (host)
- * receives each query's exact count, identical to gz_count of that query.
- * Errors: GZ_EINVAL, GZ_ENOMEM, GZ_ECUDA.
+ * one call (no paper counterpart; the merged multi-pattern program of Sec. 3 is
+ * the closest). The non-clique queries share one persistent launch over a device
+ * work queue; clique queries take the clique kernels; both kinds overlap on a
+ * small per-device stream pool and join `stream` before the call returns.
+ * out_counts[nq] (host) receives each query's exact count, identical to gz_count
+ * of that query. Errors: GZ_EINVAL, GZ_ENOMEM, GZ_ECUDA.
  */
 gz_status gz_count_batch(const gz_plan* const* plans, const gz_graph* const* graphs,
                          const int* use_orientation, int nq, void* stream,
