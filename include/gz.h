@@ -73,7 +73,9 @@ gz_status gz_load_csr(const int64_t* row_ptr, const int32_t* col_idx, int64_t n,
  * (ties broken by the original id, ascending), relabels and re-sorts every
  * list, and builds the out-list view N'(v) intersect [0, v) as a compact DAG
  * CSR. The original view is kept; counts may use either (use_orientation).
- * Idempotent. Errors: GZ_EINVAL (NULL graph), GZ_ENOMEM, GZ_ECUDA.
+ * Idempotent. Calling it again rewrites the oriented view in place (its device
+ * buffers are reused), so it first waits for all device work of the process.
+ * Errors: GZ_EINVAL (NULL graph), GZ_ENOMEM, GZ_ECUDA.
  */
 gz_status gz_orient(gz_graph* g, void* stream);
 

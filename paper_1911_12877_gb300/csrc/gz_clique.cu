@@ -531,6 +531,7 @@ int parts_for(int K, int d) {
 // heavy roots are not split.
 gz_status build_heavy_rows(GzView& v, int mo, int sms, cudaStream_t s) {
     if (v.heavy_rows_built) return GZ_OK;
+    v.heavy_rows_ok = false;
     v.heavy_off.assign(v.heavy.size(), UINT32_MAX);
     std::vector<int4> list;
     uint64_t words = 0;
@@ -547,7 +548,14 @@ gz_status build_heavy_rows(GzView& v, int mo, int sms, cudaStream_t s) {
         return GZ_OK;
     }
     int4* d_list = nullptr;
-    cudaError_t e = cudaMalloc(&v.heavy_rows, sizeof(uint32_t) * words);
+    cudaError_t e = cudaSuccess;
+    if (words > v.heavy_rows_cap) {  // grow; rebuilds of the same view reuse the buffer
+        cudaFree(v.heavy_rows);
+        v.heavy_rows = nullptr;
+        v.heavy_rows_cap = 0;
+        e = cudaMalloc(&v.heavy_rows, sizeof(uint32_t) * words);
+        if (e == cudaSuccess) v.heavy_rows_cap = words;
+    }
     if (e == cudaSuccess) e = cudaMallocAsync(&d_list, sizeof(int4) * list.size(), s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_list, list.data(), sizeof(int4) * list.size(), cudaMemcpyHostToDevice, s);
@@ -568,9 +576,11 @@ gz_status build_heavy_rows(GzView& v, int mo, int sms, cudaStream_t s) {
     if (e != cudaSuccess) {
         cudaFree(v.heavy_rows);
         v.heavy_rows = nullptr;
+        v.heavy_rows_cap = 0;
         v.heavy_off.assign(v.heavy.size(), UINT32_MAX);
         return cuda_fail(e, "clique: heavy rows");
     }
+    v.heavy_rows_ok = true;
     return GZ_OK;
 }
 
@@ -663,7 +673,7 @@ gz_status launch_k(const GzView& v, int64_t n, int64_t lo, int64_t hi, cudaStrea
     auto it = std::lower_bound(mv.heavy.begin(), mv.heavy.end(), std::make_pair((int32_t)lo, INT32_MIN));
     for (; it != mv.heavy.end() && it->first < hi; ++it) {
         const size_t i = (size_t)(it - mv.heavy.begin());
-        if (mv.heavy_rows && mv.heavy_off[i] != UINT32_MAX) hi_idx.push_back((int)i);
+        if (mv.heavy_rows_ok && mv.heavy_off[i] != UINT32_MAX) hi_idx.push_back((int)i);
     }
     std::stable_sort(hi_idx.begin(), hi_idx.end(), [&](int a, int b) {
         return mv.heavy[a].second > mv.heavy[b].second;
@@ -675,7 +685,7 @@ gz_status launch_k(const GzView& v, int64_t n, int64_t lo, int64_t hi, cudaStrea
             ent.push_back(make_int4(mv.heavy[i].first, p | (parts << 16), (int)mv.heavy_off[i], 0));
     }
     // without cached rows no root is split (the chunk slots then take them all)
-    const int heavy_d = mv.heavy_rows ? kHeavyD : mo + 1;
+    const int heavy_d = mv.heavy_rows_ok ? kHeavyD : mo + 1;
     const size_t smem = ((size_t)mo * (((mo + 31) / 32) | 1) + 2 * (size_t)mo + 1) * 4;
     int4* d_ent = nullptr;
     cudaError_t e = cudaSuccess;

@@ -437,8 +437,10 @@ gz_status build_dag(gz_graph* g, GzView* v, cudaStream_t s) {
     if (v->has_dag) return GZ_OK;
     const int64_t n = g->n;
     cudaError_t e;
-    e = cudaMalloc(&v->dag_rp, sizeof(int64_t) * (n + 1));
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc dag_rp");
+    if (!v->dag_rp) {  // kept across rebuilds of the view (same n)
+        e = cudaMalloc(&v->dag_rp, sizeof(int64_t) * (n + 1));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc dag_rp");
+    }
     unsigned long long* mx = nullptr;
     e = cudaMallocAsync(&mx, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
@@ -457,10 +459,19 @@ gz_status build_dag(gz_graph* g, GzView* v, cudaStream_t s) {
     cudaFreeAsync(mx, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "build dag: split");
-    size_t bytes = sizeof(int32_t) * (size_t)(dnnz > 0 ? dnnz : 1);
-    e = cudaMalloc(&v->dag_col, bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&v->dag_src, bytes);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc dag");
+    const int64_t need = dnnz > 0 ? dnnz : 1;
+    if (need > v->dag_cap) {  // grow; a rebuild of the same view reuses the arrays
+        cudaFree(v->dag_col);
+        cudaFree(v->dag_src);
+        v->dag_col = nullptr;
+        v->dag_src = nullptr;
+        v->dag_cap = 0;
+        const size_t bytes = sizeof(int32_t) * (size_t)need;
+        e = cudaMalloc(&v->dag_col, bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&v->dag_src, bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc dag");
+        v->dag_cap = need;
+    }
     if (n > 0) {
         k_dag_fill<<<warp_grid(n), kThreads, 0, s>>>(v->rp, v->col, v->dag_rp, n, v->dag_col, v->dag_src);
         GZ_COUNT_LAUNCH();
@@ -495,6 +506,12 @@ gz_status orient(gz_graph* g, cudaStream_t s) {
     }
     GzView& o = g->ori;
     cudaError_t e = cudaSuccess;
+    if (g->oriented) {
+        // the oriented view is rewritten in place: counts still running on other
+        // streams may read it
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(e, "gz_orient: wait for running counts");
+    }
     if (!o.rp) {
         e = cudaMalloc(&o.rp, sizeof(int64_t) * (n + 1));
         if (e == cudaSuccess) e = cudaMalloc(&o.col, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
@@ -564,16 +581,13 @@ gz_status orient(gz_graph* g, cudaStream_t s) {
             goto done;
         }
         // 4. out-list (DAG) view of the reindexed graph, rebuilt every time
-        if (o.has_dag) {
-            cudaFree(o.dag_rp); cudaFree(o.dag_col); cudaFree(o.dag_src);
-            o.dag_rp = nullptr; o.dag_col = nullptr; o.dag_src = nullptr;
+        if (o.has_dag) {  // rebuilt below into the same allocations
             o.has_dag = false;
             o.heavy.clear();
             o.heavy_built = false;
-            cudaFree(o.heavy_rows);
-            o.heavy_rows = nullptr;
             o.heavy_off.clear();
             o.heavy_rows_built = false;
+            o.heavy_rows_ok = false;
         }
         if (o.src) { cudaFree(o.src); o.src = nullptr; }
         st = build_dag(g, &o, s);

@@ -78,6 +78,7 @@ struct GzView {
     int32_t* dag_src = nullptr;  // source vertex of each out-list entry
     int32_t* src = nullptr;      // source vertex of each full-CSR entry (built on demand)
     int64_t dag_nnz = 0;
+    int64_t dag_cap = 0;         // entries dag_col / dag_src can hold (kept across rebuilds)
     int64_t max_out = 0;
     bool owned_csr = true;
     bool has_dag = false;
@@ -89,8 +90,10 @@ struct GzView {
     // kept for every later clique count of this view: heavy_off[i] is the word
     // offset of heavy[i]'s rows in heavy_rows (UINT32_MAX: none)
     uint32_t* heavy_rows = nullptr;
+    uint64_t heavy_rows_cap = 0;  // words heavy_rows can hold (kept across rebuilds)
     std::vector<uint32_t> heavy_off;
-    bool heavy_rows_built = false;
+    bool heavy_rows_built = false;  // the build has run for this out-list view
+    bool heavy_rows_ok = false;     // ... and left rows in heavy_rows
 };
 
 struct gz_graph {
