@@ -141,9 +141,20 @@ def measured_peaks():
 
 
 def kernel_source_hash():
-    """Hash of the clique kernels' source file (the kernels the roofline figures are for)."""
+    """Hash of the source of k_clique_big and the device helpers it runs (the
+    kernel the roofline figures are for); the whole file if the markers move."""
+    src = open(os.path.join(ROOT, "paper_1911_12877_gb300", "csrc", "gz_clique.cu")).read()
+    parts = []
+    for a, b in (("// Sum over the cliques that extend", "// Rows of every heavy root, built once"),
+                 ("// Roots with 32 < |O| <= max_out: one CTA per root", "// Roots whose out-list is too long")):
+        i, j = src.find(a), src.find(b)
+        if i < 0 or j < i:
+            parts = [src]
+            break
+        parts.append(src[i:j])
     h = hashlib.sha256()
-    h.update(open(os.path.join(ROOT, "paper_1911_12877_gb300", "csrc", "gz_clique.cu"), "rb").read())
+    for p in parts:
+        h.update(p.encode())
     return h.hexdigest()[:16]
 
 

@@ -213,17 +213,62 @@ __global__ void __launch_bounds__(kThreads) k_clique_rows(const int64_t* __restr
     const int Wsmax = ((max_out + 31) >> 5) | 1;
     uint32_t* rows = sm;
     int32_t* O = reinterpret_cast<int32_t*>(sm + (size_t)max_out * Wsmax);
+    // index of O: open-addressing hash of (vertex id << 32 | position), 2 *
+    // kCliqueMaxOut slots (load <= 1/2); 8-byte aligned after rows and O
+    const size_t hoff = ((size_t)max_out * Wsmax + max_out + 1) & ~(size_t)1;
+    unsigned long long* hx = reinterpret_cast<unsigned long long*>(sm + hoff);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int32_t* stage = O + max_out + (size_t)warp * kCliqueMaxOut;
+    int32_t* stage = reinterpret_cast<int32_t*>(hx + 2 * kCliqueMaxOut) + (size_t)warp * kCliqueMaxOut;
+    constexpr unsigned kMask = 2 * kCliqueMaxOut - 1;
     for (int h = blockIdx.x; h < nh; h += gridDim.x) {
         const int64_t v = hr[h].x;
         const int64_t ob = drp[v];
         const int d = (int)(drp[v + 1] - ob);
         const int Ws = ((d + 31) >> 5) | 1;
-        for (int i = threadIdx.x; i < d; i += kThreads) O[i] = dcol[ob + i];
+        for (int i = threadIdx.x; i < 2 * kCliqueMaxOut; i += kThreads) hx[i] = ~0ull;
         for (int i = threadIdx.x; i < d * Ws; i += kThreads) rows[i] = 0;
         __syncthreads();
-        build_rows(drp, dcol, O, d, rows, Ws, lane, warp, kThreads / 32, stage);
+        for (int i = threadIdx.x; i < d; i += kThreads) {
+            const int32_t x = dcol[ob + i];
+            O[i] = x;
+            const unsigned long long kv = ((unsigned long long)(uint32_t)x << 32) | (uint32_t)i;
+            unsigned sl = ((uint32_t)x * 0x9E3779B1u) >> 21;  // 11 bits: 2048 slots
+            while (atomicCAS(&hx[sl], ~0ull, kv) != ~0ull) sl = (sl + 1) & kMask;
+        }
+        __syncthreads();
+        // row(a): stream N'(O[a]) and look each entry up in the index of O (one
+        // probe instead of a binary search) when it is not much longer than a;
+        // else stage it and binary-search it for each O[b], b < a
+        for (int a = warp + 1; a < d; a += kThreads / 32) {
+            const int32_t u = O[a];
+            const int64_t ub = drp[u];
+            const int du = (int)(drp[u + 1] - ub);
+            uint32_t* ra = rows + (size_t)a * Ws;
+            if (du <= 4 * a || du > kCliqueMaxOut) {
+                for (int i = lane; i < du; i += 32) {
+                    const int32_t x = __ldg(dcol + ub + i);
+                    unsigned sl = ((uint32_t)x * 0x9E3779B1u) >> 21;
+                    int b = -1;
+                    for (;;) {
+                        const unsigned long long e = hx[sl];
+                        if (e == ~0ull) break;
+                        if ((int32_t)(e >> 32) == x) { b = (int)(uint32_t)e; break; }
+                        sl = (sl + 1) & kMask;
+                    }
+                    if (b >= 0 && b < a) atomicOr(ra + (b >> 5), 1u << (b & 31));
+                }
+            } else {
+                for (int i = lane; i < du; i += 32) stage[i] = __ldg(dcol + ub + i);
+                __syncwarp();
+                for (int b0 = 0; b0 < a; b0 += 32) {
+                    const int b = b0 + lane;
+                    const bool in = b < a && index_of(stage, du, O[b]) >= 0;
+                    const uint32_t m = __ballot_sync(kFull, in);
+                    if (lane == 0) ra[b0 >> 5] = m;
+                }
+                __syncwarp();
+            }
+        }
         __syncthreads();
         uint32_t* dst = grows + (uint32_t)hr[h].z;
         for (int i = threadIdx.x; i < d * Ws; i += kThreads) dst[i] = rows[i];
@@ -560,7 +605,8 @@ gz_status build_heavy_rows(GzView& v, int mo, int sms, cudaStream_t s) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_list, list.data(), sizeof(int4) * list.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
-        const size_t smem = ((size_t)mo * (((mo + 31) / 32) | 1) + mo + (size_t)(kThreads / 32) * kCliqueMaxOut) * 4;
+        const size_t hoff = ((size_t)mo * (((mo + 31) / 32) | 1) + mo + 1) & ~(size_t)1;
+        const size_t smem = (hoff + 2 * 2 * (size_t)kCliqueMaxOut + (size_t)(kThreads / 32) * kCliqueMaxOut) * 4;
         cudaFuncSetAttribute(k_clique_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clique_rows, kThreads, smem);
