@@ -64,6 +64,24 @@ def clique():
     _dump("clique_rmat20.json", rec)
 
 
+def clique_k5_full():
+    """The full K5 count of the k-clique workload (long: the oracle builds every
+    last-loop set), merged into clique_rmat20.json."""
+    g = S.rmat_clique()
+    go, _ = O.reindex(g)
+    path = os.path.join(HERE, "clique_rmat20.json")
+    rec = json.load(open(path))
+    assert rec["nnz"] == g.nnz
+    a, order = _plan("k5")
+    t = time.time()
+    c, e = O.count_nested(a, order, go)
+    rec["k5"]["count"] = c
+    rec["k5"]["oracle_s"] = round(time.time() - t, 1)
+    assert e == rec["k5"]["elems"]
+    print("k5", c, rec["k5"]["oracle_s"], flush=True)
+    _dump("clique_rmat20.json", rec)
+
+
 # Root ranges (reindexed ids) of the arbitrary-pattern workload, from hub blocks
 # down to low-degree blocks. Each range starts at width 1 and doubles while one
 # oracle run stays under SAMPLE_S seconds; a run that passes ATTEMPT_S is
