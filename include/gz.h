@@ -248,6 +248,30 @@ gz_status gz_count_batch(const gz_plan* const* plans, const gz_graph* const* gra
 gz_status gz_autotune(const gz_plan* p, const gz_graph* g, int use_orientation, void* stream,
                       int* block_warps, int* chunk);
 
+/* ------------------------------------------------------------------ motifs */
+
+#define GZ_MOTIF_MAX_K 6
+
+/*
+ * Motif patterns (the workload of the paper's Table 2, Sec. 7.1-7.2): every
+ * connected graph on k vertices (2 <= k <= GZ_MOTIF_MAX_K) up to isomorphism,
+ * ordered by edge count and then by canonical code; 1, 2, 6, 21 and 112 patterns
+ * for k = 2..6 (Sec. 7.2 quotes 2 on 3 vertices and 21 on 5; Sec. 1, 112 of size 6). Writes up to cap
+ * patterns as k*k uint8 adjacencies (row-major, consecutive) to adjs (may be
+ * NULL) and the number of patterns to *count. Errors: GZ_EINVAL (k out of range).
+ */
+gz_status gz_motif_patterns(int k, uint8_t* adjs, int cap, int* count);
+
+/*
+ * Motif counting: the exact vertex-induced count of every pattern of
+ * gz_motif_patterns(k), in that order, each planned like gz_plan_create and all
+ * counted in one gz_count_batch call. counts must hold the number of patterns
+ * (*count receives it; with counts NULL only *count is written).
+ * Errors: GZ_EINVAL (k out of range, cap too small), GZ_ENOMEM, GZ_ECUDA.
+ */
+gz_status gz_count_motifs(const gz_graph* g, int k, int use_orientation, void* stream,
+                          uint64_t* counts, int cap, int* count);
+
 /* --------------------------------------------------------------- serving */
 
 typedef struct {

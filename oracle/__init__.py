@@ -66,6 +66,8 @@ def _lib():
     lib.orc_elems_nested.argtypes = [I, _u8p, _i32p, L, _i64p, _i32p, L, L, I, _u64p]
     lib.orc_elems_brute.argtypes = [I, _u8p, _i32p, L, _i64p, _i32p, _u64p]
     lib.orc_reindex.argtypes = [L, _i64p, _i32p, _i64p, _i32p, _i32p]
+    lib.orc_connected_patterns.argtypes = [I, _u8p, I]
+    lib.orc_canonical_form.argtypes = [I, _u8p, _u8p]
     return lib
 
 
@@ -216,3 +218,20 @@ def reindex(g):
     _check(_lib().orc_reindex(g.n, rpp, colp, rp2.ctypes.data_as(_i64p),
                               col2.ctypes.data_as(_i32p), nid.ctypes.data_as(_i32p)), "reindex")
     return Csr(g.n, rp2, col2[:g.nnz], g.name + "_oriented"), nid[:g.n]
+
+
+def connected_patterns(k: int) -> list:
+    """Every connected k-vertex graph up to isomorphism (motif patterns, Sec. 7.1),
+    each in canonical form, by brute force over edge subsets and relabellings."""
+    n = _check(_lib().orc_connected_patterns(k, None, 0), "connected_patterns")
+    out = np.zeros(n * k * k, dtype=np.uint8)
+    _lib().orc_connected_patterns(k, out.ctypes.data_as(_u8p), n)
+    return [out[i * k * k:(i + 1) * k * k].reshape(k, k).copy() for i in range(n)]
+
+
+def canonical_form(adj) -> bytes:
+    """Canonical form of a small graph: the largest adjacency string over all relabellings."""
+    a, k, ap = _adj(adj)
+    out = np.zeros(k * k, dtype=np.uint8)
+    _check(_lib().orc_canonical_form(k, ap, out.ctypes.data_as(_u8p)), "canonical_form")
+    return out.tobytes()

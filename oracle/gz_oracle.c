@@ -33,6 +33,10 @@
  *    orc_reindex: the orientation relabelling of Sec. 6 (higher degree gets a
  *      smaller id; ties by original id, ascending).
  *
+ *  Motifs (Sec. 7.1-7.2)
+ *    orc_connected_patterns: every connected k-vertex graph up to isomorphism,
+ *      by brute force over edge subsets and all k! relabellings.
+ *
  * Readings where the paper is silent (the same list is kept in the design notes):
  *  - restriction (S[i], S[j]) in L means id(e_j) < id(e_i) (Theorem 1);
  *  - a level skips candidates equal to an already matched vertex;
@@ -689,4 +693,67 @@ int orc_reindex(int64_t n, const int64_t* rp, const int32_t* col, int64_t* rp_ou
 /* Edge test used by the tests' structural checks. */
 int orc_has_edge(const int64_t* rp, const int32_t* col, int32_t u, int32_t v) {
     return g_has_edge(rp, col, u, v);
+}
+
+/* -------------------------------------------------------------- motifs */
+
+/* Adjacency string of graph m (k x k) relabelled by p: s[i*k + j] = m[p[i]][p[j]]. */
+static void relabel(int k, const uint8_t* m, const int32_t* p, uint8_t* s) {
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) s[i * k + j] = m[p[i] * k + p[j]];
+}
+
+/*
+ * Every connected graph on k vertices up to isomorphism (the motif patterns of
+ * Sec. 7.1-7.2), plainly: each edge subset of K_k that is connected is put in its
+ * canonical form, the lexicographically largest adjacency string over all k!
+ * relabellings, and kept if that form is new. Writes up to cap canonical
+ * adjacencies (k*k bytes each) in order of discovery; returns how many.
+ */
+int orc_connected_patterns(int k, uint8_t* out, int cap) {
+    if (k < 2 || k > 6) return ORC_EINVAL;
+    const int ne = k * (k - 1) / 2;
+    int ei[15], ej[15], t = 0;
+    for (int i = 0; i < k; ++i)
+        for (int j = i + 1; j < k; ++j) { ei[t] = i; ej[t] = j; ++t; }
+    uint8_t* forms = (uint8_t*)malloc((size_t)200 * k * k);
+    if (!forms) return ORC_ENOMEM;
+    int nf = 0;
+    uint8_t m[36], best[36], cur[36];
+    for (long e = 0; e < (1L << ne); ++e) {
+        memset(m, 0, sizeof(m));
+        for (int b = 0; b < ne; ++b)
+            if (e >> b & 1) m[ei[b] * k + ej[b]] = m[ej[b] * k + ei[b]] = 1;
+        if (!pattern_ok(k, m)) continue; /* connected (and symmetric, loop-free) */
+        int32_t p[ORC_MAXK];
+        for (int i = 0; i < k; ++i) p[i] = i;
+        int have = 0;
+        do {
+            relabel(k, m, p, cur);
+            if (!have || memcmp(cur, best, (size_t)k * k) > 0) { memcpy(best, cur, (size_t)k * k); have = 1; }
+        } while (next_perm(p, k));
+        int dup = 0;
+        for (int f = 0; f < nf && !dup; ++f) dup = memcmp(forms + (size_t)f * k * k, best, (size_t)k * k) == 0;
+        if (dup) continue;
+        if (nf >= 200) { free(forms); return ORC_ECAP; }
+        memcpy(forms + (size_t)nf * k * k, best, (size_t)k * k);
+        if (out && nf < cap) memcpy(out + (size_t)nf * k * k, best, (size_t)k * k);
+        ++nf;
+    }
+    free(forms);
+    return nf;
+}
+
+/* Canonical form (as above) of one k-vertex graph, written to out (k*k bytes). */
+int orc_canonical_form(int k, const uint8_t* adj, uint8_t* out) {
+    if (k < 1 || k > ORC_MAXK) return ORC_EINVAL;
+    int32_t p[ORC_MAXK];
+    for (int i = 0; i < k; ++i) p[i] = i;
+    uint8_t cur[ORC_MAXK * ORC_MAXK];
+    int have = 0;
+    do {
+        relabel(k, adj, p, cur);
+        if (!have || memcmp(cur, out, (size_t)k * k) > 0) { memcpy(out, cur, (size_t)k * k); have = 1; }
+    } while (next_perm(p, k));
+    return 0;
 }

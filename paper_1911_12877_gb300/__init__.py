@@ -29,6 +29,7 @@ EXPORTS = [
     "gz_plan_schedules", "gz_plan_describe", "gz_plan_destroy", "gz_count", "gz_count_ex", "gz_scratch_bytes",
     "gz_count_batch", "gz_count_noalloc", "gz_autotune", "gz_server_create", "gz_server_submit", "gz_server_wait",
     "gz_server_replay", "gz_server_destroy", "gz_last_error", "gz_version", "gz_kernel_launches",
+    "gz_motif_patterns", "gz_count_motifs",
 ]
 
 
@@ -93,6 +94,8 @@ def lib() -> ctypes.CDLL:
         "gz_count_noalloc": [_P, _P, I, _P, _u64p],
         "gz_count_batch": [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(I), I, _P, _u64p],
         "gz_autotune": [_P, _P, I, _P, ctypes.POINTER(I), ctypes.POINTER(I)],
+        "gz_motif_patterns": [I, _u8p, I, ctypes.POINTER(I)],
+        "gz_count_motifs": [_P, I, I, _P, _u64p, I, ctypes.POINTER(I)],
         "gz_server_create": [ctypes.POINTER(ServerOpts), ctypes.POINTER(_P)],
         "gz_server_submit": [_P, _P, _P, I, _i64p],
         "gz_server_wait": [_P, I64, I64, _u64p, _i64p],
@@ -318,6 +321,27 @@ def autotune(plan: Plan, graph: Graph, orientation: bool = False, stream=None):
     _check(lib().gz_autotune(plan.handle, graph.handle, int(orientation), _stream(stream),
                              ctypes.byref(bw), ctypes.byref(ch)), "gz_autotune")
     return bw.value, ch.value
+
+
+def motif_patterns(k: int) -> list:
+    """Every connected k-vertex pattern up to isomorphism (gz_motif_patterns)."""
+    cnt = ctypes.c_int()
+    _check(lib().gz_motif_patterns(k, None, 0, ctypes.byref(cnt)), "gz_motif_patterns")
+    buf = np.zeros(max(cnt.value, 1) * k * k, dtype=np.uint8)
+    _check(lib().gz_motif_patterns(k, buf.ctypes.data_as(_u8p), cnt.value, ctypes.byref(cnt)),
+           "gz_motif_patterns")
+    return [buf[i * k * k:(i + 1) * k * k].reshape(k, k).copy() for i in range(cnt.value)]
+
+
+def count_motifs(graph: Graph, k: int, orientation: bool = False, stream=None) -> list[int]:
+    """Exact counts of every connected k-vertex pattern, in motif_patterns(k) order."""
+    cnt = ctypes.c_int()
+    _check(lib().gz_count_motifs(graph.handle, k, int(orientation), _stream(stream), None, 0,
+                                 ctypes.byref(cnt)), "gz_count_motifs")
+    out = (ctypes.c_uint64 * max(cnt.value, 1))()
+    _check(lib().gz_count_motifs(graph.handle, k, int(orientation), _stream(stream), out, cnt.value,
+                                 ctypes.byref(cnt)), "gz_count_motifs")
+    return list(out)[: cnt.value]
 
 
 class Server:

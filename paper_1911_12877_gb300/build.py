@@ -17,8 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libgz.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["gz_api.cpp", "gz_plan.cpp", "gz_server.cpp", "gz_graph.cu", "gz_count.cu",
-           "gz_clique.cu", "gz_noalloc.cu"]
+SOURCES = ["gz_api.cpp", "gz_plan.cpp", "gz_server.cpp", "gz_motif.cpp", "gz_graph.cu",
+           "gz_count.cu", "gz_clique.cu", "gz_noalloc.cu"]
 
 
 def _nvcc() -> str:

@@ -347,3 +347,30 @@ def test_server_wait_statuses():
         srv.wait(987654, timeout_ms=0)
     assert e.value.status == gz.GZ_EINVAL
     srv.close()
+
+
+@pytest.mark.parametrize("k", [3, 4, 5])
+def test_count_motifs_against_oracle(k):
+    """Motif counting (every connected k-vertex pattern, Sec. 7.1-7.2): each count
+    equals the oracle's, and on a tiny graph the counts add up to the number of
+    connected induced k-vertex subgraphs, found by brute force."""
+    import itertools
+    pats = gz.motif_patterns(k)
+    for g in [S.random_small(14, 0.35, 61), S.rmat(9, 8, 62)]:
+        G = gz.Graph.from_csr(g).orient()
+        got = gz.count_motifs(G, k, orientation=True)
+        assert got == gz.count_motifs(G, k, orientation=False)
+        assert got == [oracle_count(a, g) for a in pats]
+        if g.n <= 14:
+            nb = [set(g.neighbors(v).tolist()) for v in range(g.n)]
+            conn = 0
+            for sub in itertools.combinations(range(g.n), k):
+                seen, todo = {sub[0]}, [sub[0]]
+                while todo:
+                    v = todo.pop()
+                    for u in sub:
+                        if u not in seen and u in nb[v]:
+                            seen.add(u)
+                            todo.append(u)
+                conn += len(seen) == k
+            assert sum(got) == conn

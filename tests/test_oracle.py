@@ -329,3 +329,26 @@ def test_planted_mistakes_are_caught(mutation):
     finally:
         O.set_mutation("none")
     assert _pins_pass()
+
+
+# ------------------------------------------------------------------ motif patterns
+
+def test_motif_pattern_counts():
+    # Sec. 7.2: 2 patterns on 3 vertices, 21 on 5; Sec. 1: 112 size-6 patterns
+    assert [len(O.connected_patterns(k)) for k in (3, 5, 6)] == [2, 21, 112]
+    # the connected graphs on 3 and 4 vertices are exactly the named ones
+    for k, names in [(3, ["wedge", "triangle"]),
+                     (4, ["path4", "star3", "c4", "paw", "diamond", "k4"])]:
+        forms = {O.canonical_form(a) for a in O.connected_patterns(k)}
+        assert forms == {O.canonical_form(adjacency(n)) for n in names}
+        assert len(forms) == len(names)
+
+
+def test_motif_patterns_are_connected_and_distinct():
+    for k in (4, 5):
+        pats = O.connected_patterns(k)
+        forms = [O.canonical_form(a) for a in pats]
+        assert len(set(forms)) == len(pats)
+        for a in pats:
+            assert (a == a.T).all() and not a.diagonal().any()
+            assert len(O.automorphisms(a)) >= 1  # the oracle accepts it as a connected pattern

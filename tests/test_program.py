@@ -257,3 +257,12 @@ def test_clique_program_is_chain_of_out_list_intersections():
         assert op["left_iter"] == 1
         assert all(r[1] == 0 and r[2] == 2 for r in op["rights"])
     assert all(v == 1 for v in prog["buf"].values())
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 5, 6])
+def test_motif_patterns_match_oracle(k):
+    """The library's motif patterns (host enumeration) are the oracle's, up to
+    isomorphism, with no repeats."""
+    mine = [O.canonical_form(a) for a in gz.motif_patterns(k)]
+    assert len(mine) == len(set(mine))
+    assert set(mine) == {O.canonical_form(a) for a in O.connected_patterns(k)}
