@@ -103,12 +103,35 @@ void forget_plan(const gz_plan* p) {
     for (auto it = m.begin(); it != m.end();) it = it->first.p == p ? m.erase(it) : std::next(it);
 }
 
+// ------------------------------------------------------------ device setup
+
+// Once per device: the stream-ordered pool the library allocates its per-call
+// buffers from keeps freed memory for reuse instead of returning it at every
+// synchronisation (the default), so a count's allocations cost no new mappings.
+// This sets an attribute of this process's memory pool only.
+void device_setup() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done[dev] = true;
+}
+
 // ------------------------------------------------------------ query preparation
 
 // Picks the view, builds the out-list / unit arrays it needs, and turns a root
 // range into a unit (edge) range.
 gz_status prepare_query(const gz_plan* p, const gz_graph* gc, int use_orientation, int64_t root_lo,
                         int64_t root_hi, cudaStream_t s, Query& q) {
+    device_setup();
     gz_graph* g = const_cast<gz_graph*>(gc);
     if (use_orientation && !g->oriented) {
         set_error("count: use_orientation = 1 needs gz_orient first");
@@ -331,6 +354,7 @@ uint64_t gz_kernel_launches(void) { return g_launches.load(); }
 
 gz_status gz_load_csr(const int64_t* row_ptr, const int32_t* col_idx, int64_t n, int64_t nnz,
                       int device_ptrs, uint32_t flags, void* stream, gz_graph** out) {
+    device_setup();
     if (!out) { set_error("gz_load_csr: out is NULL"); return GZ_EINVAL; }
     *out = nullptr;
     if (n < 0 || nnz < 0 || !row_ptr || (nnz > 0 && !col_idx)) {

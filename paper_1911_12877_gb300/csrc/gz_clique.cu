@@ -12,9 +12,13 @@
 //
 //  - k_clique_small: one warp per root with |O| <= 32 (one 32-bit row per lane's
 //    vertex, rows in shared memory).
-//  - k_clique_big: one CTA per root with 32 < |O| <= kCliqueMaxOut; rows built
-//    cooperatively (each row streams the shorter of O[0, a) and N(O[a])),
-//    then the (a, b) pairs of the local DAG are spread over all threads.
+//  - k_clique_big: one 512-thread CTA per root with 32 < |O| <= kCliqueMaxOut,
+//    rows in shared memory (odd word stride), then the (a, b) edges of the
+//    local DAG spread over all threads. Roots with |O| >= kHeavyD are split
+//    over several CTAs ("parts"); their rows are built once per out-list view
+//    by k_clique_rows into device memory and copied by each part.
+//  - k_clique_long: roots with kCliqueMaxOut < |O| <= kCliqueLongOut, rows in
+//    device memory (k_clique_long_rows); longer roots are left to the caller.
 #include <algorithm>
 #include <climits>
 #include <cmath>

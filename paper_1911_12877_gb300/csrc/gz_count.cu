@@ -12,7 +12,11 @@
 //    an explicit DFS. Each set operation streams its left list 32 elements at a
 //    time (coalesced), probes every right list by binary search, and either
 //    compacts the survivors into the warp's scratch buffer (ballot + popc) or,
-//    on the last loop, only counts them.
+//    on the last loop, only counts them. The last loop is flattened across the
+//    candidates of the loop before it (fixed operands hashed in shared memory
+//    or in warp scratch; subtraction-only shapes counted by inclusion-exclusion).
+//  - Edges with many loop-2 candidates are deferred by the first pass and run
+//    in chunks of candidates by a second pass (k_enumerate_split).
 //  - Counts are per-lane uint64, reduced by warp shuffles and added to the
 //    query's slot with one atomic per warp per query. Integer adds are exact and
 //    order-independent, so the result is bit-exact whatever the schedule.
