@@ -14,7 +14,7 @@ import oracle as O
 import synthetic as S
 from synthetic.patterns import EDGES, adjacency
 
-SURVEY_TABLE = {
+SCHEDULE_TABLE = {
     # pattern: (|Aut|, valid schedules K, distinct schedules K/|Aut|)
     "wedge": (2, 4, 2), "triangle": (6, 6, 1), "path4": (2, 8, 4), "star3": (6, 12, 2),
     "c4": (8, 16, 2), "paw": (2, 14, 7), "diamond": (4, 20, 5), "k4": (24, 24, 1),
@@ -56,10 +56,10 @@ def test_automorphisms_preserve_structure():
             assert (a[np.ix_(x, x)] == a).all()
 
 
-@pytest.mark.parametrize("name", sorted(SURVEY_TABLE))
+@pytest.mark.parametrize("name", sorted(SCHEDULE_TABLE))
 def test_schedule_counts(name):
     a = adjacency(name)
-    aut, K, D = SURVEY_TABLE[name]
+    aut, K, D = SCHEDULE_TABLE[name]
     assert len(O.automorphisms(a)) == aut
     valid = O.valid_schedules_brute(a)
     assert len(valid) == K
@@ -314,7 +314,7 @@ def _pins_pass():
         for name in ["house", "triangle", "k4"]:
             test_elems_match_brute_definition(name)
         test_reindex_orders_by_degree(1)
-        for k in SURVEY_TABLE:
+        for k in SCHEDULE_TABLE:
             test_schedule_counts(k)
     except AssertionError:
         return False
