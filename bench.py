@@ -587,7 +587,7 @@ def run_served(args, dist, world, rank, local):
         gidx = np.zeros(nreq, np.int32)
         rec = {}
         for mode in ("served", "fifo"):
-            srv = gz.Server(max_inflight=args.inflight, max_batch=args.max_batch)
+            srv = gz.Server(max_inflight=args.inflight, max_batch=args.max_batch, heavy_ms=args.heavy_ms)
             counts, lat, st = srv.replay(plans, [G], [1] * nreq, arr, pidx, gidx, fifo=(mode == "fifo"))
             srv.close()
             if [int(c) for c in counts] != [alone[i] for i in pidx]:
@@ -659,6 +659,8 @@ def main(argv=None):
     ap.add_argument("--rates", default="12.5,25,50,100,200", help="served config: Poisson rates")
     ap.add_argument("--inflight", type=int, default=2, help="served config: concurrent launches")
     ap.add_argument("--max-batch", type=int, default=8, help="served config: requests per launch")
+    ap.add_argument("--heavy-ms", type=float, default=0.0,
+                    help="served config: slow-request threshold in ms (0: library default, <0: off)")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "gz":
         args.warmup = 3

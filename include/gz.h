@@ -278,12 +278,17 @@ typedef struct {
     int max_inflight_launches; /* concurrent batched launches (streams), >= 1 */
     int max_batch;             /* queries per launch */
     uint64_t scratch_budget;   /* device bytes for in-flight scratch, 0 = 4 GiB */
+    double heavy_ms;           /* slow-request threshold (ms), 0 = 20, < 0 = none */
 } gz_server_opts;
 
 /*
  * Continuous-batching request loop over device-resident graphs. Requests are
  * admitted as launch slots and scratch memory free up, batched with whatever
- * else is waiting, and run on separate streams so their work overlaps.
+ * else is waiting, and run on separate streams so their work overlaps. The loop
+ * keeps a moving average of each (plan, graph)'s service time when it runs
+ * alone; a request above heavy_ms (or not yet measured) is launched by itself,
+ * with at most one such launch in flight, and faster requests are batched
+ * around it.
  */
 gz_status gz_server_create(const gz_server_opts* opts, gz_server** out);
 

@@ -53,6 +53,15 @@ struct Slot {
     std::vector<Req*> batch;
     uint64_t scratch = 0;
     bool busy = false;
+    bool heavy = false;              // runs one slow request alone
+    Clock::time_point t_launch;
+};
+
+// Observed service time of a (plan, graph) pair, from launches that ran it alone.
+struct CostKey {
+    const gz_plan* p;
+    const gz_graph* g;
+    bool operator<(const CostKey& o) const { return p != o.p ? p < o.p : g < o.g; }
 };
 
 }  // namespace
@@ -72,6 +81,7 @@ struct gz_server {
     int64_t max_queue = 0;
     int device = 0;
     std::atomic<int> fatal{0};
+    std::map<CostKey, double> cost_ms;  // moving average per (plan, graph)
 };
 
 namespace {
@@ -144,30 +154,55 @@ void worker_main(gz_server* s) {
                 r->done = true;
             }
             if (q != cudaSuccess) cudaGetLastError();
+            if (nq == 1 && q == cudaSuccess) {
+                const double ms = std::chrono::duration<double, std::milli>(now - sl.t_launch).count();
+                double& c = s->cost_ms[CostKey{sl.batch[0]->plan, sl.batch[0]->graph}];
+                c = c > 0 ? 0.7 * c + 0.3 * ms : ms;
+            }
             s->inflight_scratch -= sl.scratch;
             sl.batch.clear();
             sl.busy = false;
+            sl.heavy = false;
             progress = true;
             s->cv_done.notify_all();
         }
-        // 2. admission into free slots
+        // 2. admission into free slots. A request whose (plan, graph) has run
+        //    alone for longer than heavy_ms (or has not run yet) is "slow": it
+        //    is launched by itself and at most one slow launch is in flight, so
+        //    slow requests do not share the GPU with each other; fast requests
+        //    are batched in arrival order around them.
+        const double heavy_ms = s->opts.heavy_ms > 0 ? s->opts.heavy_ms : 20.0;
+        auto slow = [&](const Req* r) {
+            if (s->opts.heavy_ms < 0) return false;  // class-blind admission
+            auto it = s->cost_ms.find(CostKey{r->plan, r->graph});
+            return it == s->cost_ms.end() || it->second > heavy_ms;
+        };
         for (Slot& sl : s->slots) {
             if (sl.busy || s->pending.empty()) continue;
+            bool heavy_busy = false;
+            for (const Slot& o : s->slots) heavy_busy = heavy_busy || (o.busy && o.heavy);
             const uint64_t budget = s->opts.scratch_budget;
             uint64_t used = 0;
-            while (!s->pending.empty() && (int)sl.batch.size() < sl.cap) {
-                Req* r = s->pending.front();
+            for (auto it = s->pending.begin(); it != s->pending.end() && (int)sl.batch.size() < sl.cap;) {
+                Req* r = *it;
+                const bool rs = slow(r);
+                if (rs && (heavy_busy || !sl.batch.empty())) { ++it; continue; }
                 uint64_t need = std::max(used, r->scratch);  // a batch needs its largest query's scratch
                 if (!sl.batch.empty() && s->inflight_scratch + need > budget) break;
                 if (sl.batch.empty() && s->inflight_scratch + need > budget && s->inflight_scratch > 0) break;
                 used = need;
                 sl.batch.push_back(r);
-                s->pending.pop_front();
+                it = s->pending.erase(it);
+                if (rs) {  // a slow request runs alone
+                    sl.heavy = true;
+                    break;
+                }
             }
             if (sl.batch.empty()) continue;
             sl.scratch = used;
             s->inflight_scratch += used;
             sl.busy = true;
+            sl.t_launch = Clock::now();
             s->launches++;
             lk.unlock();
             gz_status st = launch_batch(s, sl);
