@@ -422,8 +422,10 @@ gz_status gz_graph_info(const gz_graph* g, gz_graph_stats* out) {
     auto view_bytes = [&](const GzView& v, bool csr) {
         int64_t x = 0;
         if (csr && v.rp) x += 8 * (g->n + 1) + 4 * g->nnz;
-        if (v.has_dag) x += 8 * (g->n + 1) + 8 * v.dag_nnz;
+        if (v.dag_rp) x += 8 * (g->n + 1);
+        x += 8 * v.dag_cap;  // dag_col + dag_src
         if (v.src) x += 4 * g->nnz;
+        x += 4 * (int64_t)v.heavy_rows_cap;  // cached clique rows
         return x;
     };
     b += view_bytes(g->orig, g->orig.owned_csr);
