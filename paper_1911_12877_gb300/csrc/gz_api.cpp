@@ -354,6 +354,7 @@ uint64_t gz_kernel_launches(void) { return g_launches.load(); }
 
 gz_status gz_load_csr(const int64_t* row_ptr, const int32_t* col_idx, int64_t n, int64_t nnz,
                       int device_ptrs, uint32_t flags, void* stream, gz_graph** out) {
+    GZ_RANGE("gz_load_csr");
     device_setup();
     if (!out) { set_error("gz_load_csr: out is NULL"); return GZ_EINVAL; }
     *out = nullptr;
@@ -401,6 +402,7 @@ gz_status gz_load_csr(const int64_t* row_ptr, const int32_t* col_idx, int64_t n,
 }
 
 gz_status gz_orient(gz_graph* g, void* stream) {
+    GZ_RANGE("gz_orient");
     if (!check_graph(g, "gz_orient")) return GZ_EINVAL;
     return gz::orient(g, (cudaStream_t)stream);
 }
@@ -507,6 +509,7 @@ gz_status gz_pattern_named(const char* name, int* k, uint8_t* adj) {
 }
 
 gz_status gz_plan_create(int k, const uint8_t* adj, uint32_t flags, gz_plan** out) {
+    GZ_RANGE("gz_plan_create");
     (void)flags;
     return make_plan(k, adj, nullptr, out);
 }
@@ -567,6 +570,7 @@ void gz_plan_destroy(gz_plan* p) {
 
 gz_status gz_count_ex(const gz_plan* p, const gz_graph* g, const gz_count_opts* opts, void* stream,
                       uint64_t* out_count) {
+    GZ_RANGE("gz_count");
     if (!p || !check_graph(g, "gz_count") || !out_count) {
         if (!p) set_error("gz_count: plan is NULL");
         if (!out_count) set_error("gz_count: out_count is NULL");
@@ -613,6 +617,7 @@ gz_status gz_scratch_bytes(const gz_plan* p, const gz_graph* g, int use_orientat
 
 gz_status gz_count_batch(const gz_plan* const* plans, const gz_graph* const* graphs,
                          const int* use_orientation, int nq, void* stream, uint64_t* out_counts) {
+    GZ_RANGE("gz_count_batch");
     if (nq < 0 || (nq > 0 && (!plans || !graphs || !out_counts))) {
         set_error("gz_count_batch: bad arguments");
         return GZ_EINVAL;

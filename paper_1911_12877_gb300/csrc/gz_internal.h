@@ -6,6 +6,7 @@
 #include <utility>
 #include <vector>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/gz.h"
 
@@ -106,6 +107,18 @@ struct gz_graph {
 };
 
 namespace gz {
+
+// NVTX range around one library call (shows up in Nsight timelines; a no-op
+// without a profiler attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define GZ_CAT2(a, b) a##b
+#define GZ_CAT(a, b) GZ_CAT2(a, b)
+#define GZ_RANGE(name) ::gz::NvtxRange GZ_CAT(gz_range_, __LINE__)(name)
 
 // Kernels this library has launched in this process (for launch accounting).
 extern std::atomic<unsigned long long> g_launches;

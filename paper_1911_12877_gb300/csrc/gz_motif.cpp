@@ -127,6 +127,7 @@ gz_status gz_motif_patterns(int k, uint8_t* adjs, int cap, int* count) {
 
 gz_status gz_count_motifs(const gz_graph* g, int k, int use_orientation, void* stream,
                           uint64_t* counts, int cap, int* count) {
+    GZ_RANGE("gz_count_motifs");
     if (!g || !count) {
         set_error("gz_count_motifs: NULL argument");
         return GZ_EINVAL;

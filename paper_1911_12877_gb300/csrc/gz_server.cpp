@@ -100,6 +100,7 @@ uint64_t req_scratch(const Req* r) {
 
 // Launches slot.batch on slot.stream; called with the lock released.
 gz_status launch_batch(gz_server* s, Slot& sl) {
+    GZ_RANGE("gz_server_launch");
     const int nq = (int)sl.batch.size();
     std::vector<Query> qs(nq);
     for (int i = 0; i < nq; ++i) {
