@@ -250,6 +250,8 @@ def run_clique(args, dist, world, rank, local):
         counts = step()
     if counts[0] != gold["k4"]["count"]:
         raise SystemExit(f"K4 count {counts[0]} != oracle {gold['k4']['count']}")
+    if "count" in gold["k5"] and counts[1] != gold["k5"]["count"]:
+        raise SystemExit(f"K5 count {counts[1]} != oracle {gold['k5']['count']}")
     barrier(dist)
     torch.cuda.synchronize()
     launches0 = gz.kernel_launches()
