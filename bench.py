@@ -514,6 +514,22 @@ def run_patterns(args, dist, world, rank, local):
         if name in full:
             c, ms = _time_counts(lambda: gz.count(p, G, orientation=True), args.steps, stream)
             r["full"] = {"count": c, **_summary(ms)}
+        if args.measured and gold and name in gold["patterns"]:
+            # measured schedule selection on the two lowest-degree sample blocks
+            # (cut to 256 roots), then the chosen plan on every sample range
+            samp = [(lo, min(hi, lo + 256)) for lo, hi, _, _ in gold["patterns"][name]["samples"][-2:]]
+            pm, best_ms, model_ms = gz.plan_measured(gz.pattern_named(name), G, samp)
+            ms_m = 0.0
+            for lo, hi, want, e in gold["patterns"][name]["samples"]:
+                got, ms = _time_counts(lambda: gz.count(pm, G, True, lo, hi), args.steps, stream)
+                if got != want:
+                    raise SystemExit(f"{name} (measured schedule) roots [{lo},{hi}): {got} != oracle {want}")
+                ms_m += statistics.median(ms)
+            r["measured_schedule"] = {"order": pm.info()["order"], "model_order": p.info()["order"],
+                                      "selection_samples": samp, "selection_ms": round(best_ms, 3),
+                                      "model_selection_ms": round(model_ms, 3),
+                                      "sampled_ms": round(ms_m, 3),
+                                      "model_sampled_ms": r.get("sampled", {}).get("ms")}
         res[name] = r
     launches = gz.kernel_launches() - l0
     value = tot_e / (tot_ms / 1e3) if tot_ms > 0 else None
@@ -655,6 +671,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scale", type=int, default=0, help="R-MAT scale override (smaller cases)")
     ap.add_argument("--patterns", default="", help="patterns config: comma-separated subset")
+    ap.add_argument("--measured", action="store_true",
+                    help="patterns config: also select each pattern's schedule by timing (NEXT f3)")
     ap.add_argument("--full", default="", help="patterns config: patterns whose full count is timed "
                     "(default none at scale 22, all below)")
     ap.add_argument("--requests", type=int, default=300, help="served config: requests per rate")

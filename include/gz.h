@@ -146,6 +146,22 @@ gz_status gz_plan_info(const gz_plan* p, int* k, int32_t* order, int32_t* bound_
 gz_status gz_plan_schedules(int k, const uint8_t* adj, int32_t* orders, int cap, int* count);
 
 /*
+ * Measured schedule selection: the Sec. 5.4 performance model ranks schedules
+ * on a uniform random graph (n = 1000, degree 5); this instead times every
+ * distinct schedule (Algorithm 4) on the given graph, counting the roots of the
+ * nsample ranges [sample_lo[i], sample_hi[i]) (ids of the view counted), and
+ * plans the fastest (first on ties). A schedule whose running time passes 4x
+ * the best total so far is dropped between ranges. The count does not depend
+ * on the schedule, only the time does. *best_ms (optional) receives the chosen
+ * schedule's time on the samples, *model_ms (optional) that of the schedule
+ * gz_plan_create would pick. Errors: as gz_plan_create and gz_count_ex.
+ */
+gz_status gz_plan_create_measured(int k, const uint8_t* adj, const gz_graph* g,
+                                  int use_orientation, const int64_t* sample_lo,
+                                  const int64_t* sample_hi, int nsample, void* stream,
+                                  gz_plan** out, double* best_ms, double* model_ms);
+
+/*
  * Text listing of the compiled nested-loop program (one line per item, NUL
  * terminated, truncated to cap bytes): "unit dag=D flat=F" (F: how the last loop is
  * flattened across the candidates of loop k-2; 0 = not), then per loop t its set

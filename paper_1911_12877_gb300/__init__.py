@@ -29,7 +29,7 @@ EXPORTS = [
     "gz_plan_schedules", "gz_plan_describe", "gz_plan_destroy", "gz_count", "gz_count_ex", "gz_scratch_bytes",
     "gz_count_batch", "gz_count_noalloc", "gz_autotune", "gz_server_create", "gz_server_submit", "gz_server_wait",
     "gz_server_replay", "gz_server_destroy", "gz_last_error", "gz_version", "gz_kernel_launches",
-    "gz_motif_patterns", "gz_count_motifs",
+    "gz_motif_patterns", "gz_count_motifs", "gz_plan_create_measured",
 ]
 
 
@@ -95,6 +95,8 @@ def lib() -> ctypes.CDLL:
         "gz_count_batch": [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(I), I, _P, _u64p],
         "gz_autotune": [_P, _P, I, _P, ctypes.POINTER(I), ctypes.POINTER(I)],
         "gz_motif_patterns": [I, _u8p, I, ctypes.POINTER(I)],
+        "gz_plan_create_measured": [I, _u8p, _P, I, _i64p, _i64p, I, _P, ctypes.POINTER(_P),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
         "gz_count_motifs": [_P, I, I, _P, _u64p, I, ctypes.POINTER(I)],
         "gz_server_create": [ctypes.POINTER(ServerOpts), ctypes.POINTER(_P)],
         "gz_server_submit": [_P, _P, _P, I, _i64p],
@@ -201,6 +203,24 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def plan_measured(adj, graph: "Graph", samples, orientation: bool = True, stream=None):
+    """The fastest distinct schedule of the pattern on graph, timed on the root
+    ranges samples = [(lo, hi), ...]; returns (Plan, best_ms, model_ms)."""
+    a, k = _adj(adj)
+    lo = np.ascontiguousarray([s[0] for s in samples], dtype=np.int64)
+    hi = np.ascontiguousarray([s[1] for s in samples], dtype=np.int64)
+    h = _P()
+    best, model = ctypes.c_double(), ctypes.c_double()
+    _check(lib().gz_plan_create_measured(k, a.ctypes.data_as(_u8p), graph.handle, int(orientation),
+                                         lo.ctypes.data_as(_i64p), hi.ctypes.data_as(_i64p), len(samples),
+                                         _stream(stream), ctypes.byref(h), ctypes.byref(best),
+                                         ctypes.byref(model)), "gz_plan_create_measured")
+    p = Plan.__new__(Plan)
+    p._a = a
+    p.handle = h
+    return p, best.value, model.value
 
 
 def schedules(adj) -> np.ndarray:

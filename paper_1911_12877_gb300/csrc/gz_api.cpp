@@ -530,6 +530,76 @@ gz_status gz_plan_info(const gz_plan* p, int* k, int32_t* order, int32_t* bound_
     return GZ_OK;
 }
 
+gz_status gz_plan_create_measured(int k, const uint8_t* adj, const gz_graph* g,
+                                  int use_orientation, const int64_t* sample_lo,
+                                  const int64_t* sample_hi, int nsample, void* stream,
+                                  gz_plan** out, double* best_ms, double* model_ms) {
+    GZ_RANGE("gz_plan_create_measured");
+    if (!out || !check_graph(g, "gz_plan_create_measured") || nsample < 1 || !sample_lo || !sample_hi) {
+        set_error("gz_plan_create_measured: bad arguments");
+        return GZ_EINVAL;
+    }
+    *out = nullptr;
+    int ns = 0;
+    gz_status st = list_schedules(k, adj, nullptr, 0, &ns);
+    if (st != GZ_OK) return st;
+    std::vector<int32_t> orders((size_t)ns * k);
+    list_schedules(k, adj, orders.data(), ns, &ns);
+    gz_plan* model = nullptr;
+    st = make_plan(k, adj, nullptr, &model);
+    if (st != GZ_OK) return st;
+    auto time_plan = [&](const gz_plan* p, double cutoff, double* ms) -> gz_status {
+        double total = 0.0;
+        for (int i = 0; i < nsample; ++i) {
+            gz_count_opts o{};
+            o.use_orientation = use_orientation;
+            o.root_lo = sample_lo[i];
+            o.root_hi = sample_hi[i];
+            uint64_t c = 0;
+            const auto t0 = std::chrono::steady_clock::now();
+            gz_status r = gz_count_ex(p, g, &o, stream, &c);  // synchronous
+            if (r != GZ_OK) return r;
+            total += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            if (total > cutoff) break;
+        }
+        *ms = total;
+        return GZ_OK;
+    };
+    // warm the views the plans need, then time the model's choice first
+    double mms = 0.0;
+    st = time_plan(model, 1e300, &mms);
+    if (st == GZ_OK) st = time_plan(model, 1e300, &mms);
+    double best = mms;
+    int besti = -1;  // -1: the model's plan
+    for (int i = 0; i < ns && st == GZ_OK; ++i) {
+        if (memcmp(orders.data() + (size_t)i * k, model->order, sizeof(int32_t) * k) == 0) continue;
+        gz_plan* p = nullptr;
+        st = make_plan(k, adj, orders.data() + (size_t)i * k, &p);
+        if (st != GZ_OK) break;
+        double ms = 0.0;
+        st = time_plan(p, 4.0 * best, &ms);
+        gz_plan_destroy(p);
+        if (st == GZ_OK && ms < best) {
+            best = ms;
+            besti = i;
+        }
+    }
+    if (st != GZ_OK) {
+        gz_plan_destroy(model);
+        return st;
+    }
+    if (besti < 0) {
+        *out = model;
+    } else {
+        gz_plan_destroy(model);
+        st = make_plan(k, adj, orders.data() + (size_t)besti * k, out);
+        if (st != GZ_OK) return st;
+    }
+    if (best_ms) *best_ms = best;
+    if (model_ms) *model_ms = mms;
+    return GZ_OK;
+}
+
 gz_status gz_plan_schedules(int k, const uint8_t* adj, int32_t* orders, int cap, int* count) {
     return list_schedules(k, adj, orders, cap, count);
 }

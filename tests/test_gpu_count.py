@@ -391,3 +391,17 @@ def test_counts_survive_reorientation():
     H = gz.Graph.from_csr(g).orient()
     assert [gz.count(gz.Plan(n), H, True) for n in names] == before
     assert before[:2] == [oracle_count("k4", g), oracle_count("k5", g)]
+
+
+@pytest.mark.parametrize("name", ["paw", "diamond", "house", "chordal5"])
+def test_measured_schedule_keeps_counts(name):
+    """Measured schedule selection picks one of Algorithm 4's distinct schedules
+    by timing them on sample roots; the count must not depend on the choice."""
+    g = S.rmat(11, 8, 64)
+    G = gz.Graph.from_csr(g).orient()
+    a = adjacency(name)
+    p, best_ms, model_ms = gz.plan_measured(a, G, [(100, 164), (1000, 1256)])
+    assert best_ms <= model_ms + 1e-9
+    order = p.info()["order"]
+    assert any(list(s) == order for s in O.distinct_schedules(a))
+    assert gz.count(p, G, True) == oracle_count(a, g)
