@@ -514,22 +514,6 @@ def run_patterns(args, dist, world, rank, local):
         if name in full:
             c, ms = _time_counts(lambda: gz.count(p, G, orientation=True), args.steps, stream)
             r["full"] = {"count": c, **_summary(ms)}
-        if args.measured and gold and name in gold["patterns"]:
-            # measured schedule selection on the two lowest-degree sample blocks
-            # (cut to 256 roots), then the chosen plan on every sample range
-            samp = [(lo, min(hi, lo + 256)) for lo, hi, _, _ in gold["patterns"][name]["samples"][-2:]]
-            pm, best_ms, model_ms = gz.plan_measured(gz.pattern_named(name), G, samp)
-            ms_m = 0.0
-            for lo, hi, want, e in gold["patterns"][name]["samples"]:
-                got, ms = _time_counts(lambda: gz.count(pm, G, True, lo, hi), args.steps, stream)
-                if got != want:
-                    raise SystemExit(f"{name} (measured schedule) roots [{lo},{hi}): {got} != oracle {want}")
-                ms_m += statistics.median(ms)
-            r["measured_schedule"] = {"order": pm.info()["order"], "model_order": p.info()["order"],
-                                      "selection_samples": samp, "selection_ms": round(best_ms, 3),
-                                      "model_selection_ms": round(model_ms, 3),
-                                      "sampled_ms": round(ms_m, 3),
-                                      "model_sampled_ms": r.get("sampled", {}).get("ms")}
         res[name] = r
     launches = gz.kernel_launches() - l0
     value = tot_e / (tot_ms / 1e3) if tot_ms > 0 else None
@@ -655,8 +639,90 @@ def run_motifs(args, dist, world, rank, local):
                  paper_context="Table 2: CiteSeer motif-3/4/5 in 0.9 / 2.4 / 38 ms on 2x8 Xeon cores")
 
 
+SCHEDULE_PATTERNS = ["wedge", "path4", "star3", "c4", "paw", "diamond", "c5", "house", "hourglass",
+                     "chordal5", "chordal6"]
+
+
+def _r2_loglog(x, y):
+    """R^2 of the least-squares line through (log x, log y)."""
+    lx, ly = np.log(np.asarray(x, float)), np.log(np.asarray(y, float))
+    if len(lx) < 3 or np.ptp(lx) == 0 or np.ptp(ly) == 0:
+        return None
+    r = np.corrcoef(lx, ly)[0, 1]
+    return float(r * r)
+
+
+def _spearman(x, y):
+    if len(x) < 3:
+        return None
+    rx = np.argsort(np.argsort(x)).astype(float)
+    ry = np.argsort(np.argsort(y)).astype(float)
+    if np.ptp(rx) == 0 or np.ptp(ry) == 0:
+        return None
+    return float(np.corrcoef(rx, ry)[0, 1])
+
+
+def run_schedules(args, dist, world, rank, local):
+    """Measured schedule selection against the Sec. 5.4 performance model (the
+    synthetic analogue of Fig. 11): every distinct schedule (Algorithm 4) of each
+    pattern counts the whole oriented R-MAT graph (scale 14 ef 16 seed 14 by
+    default) through gz_schedule_times; a schedule past --cutoff x the best is
+    dropped. All kept schedules must give the same count. Reported per pattern:
+    the model's pick and its time against the fastest, the rank correlation and
+    the log-log R^2 of estimated cost against time."""
+    import torch
+    import paper_1911_12877_gb300 as gz
+    import synthetic as S
+    torch.cuda.set_device(local)
+    scale = args.scale or 14
+    g = S.rmat(scale, 16, scale)
+    G = gz.Graph.from_csr(g).orient()
+    names = args.patterns.split(",") if args.patterns else SCHEDULE_PATTERNS
+    whole = [(0, g.n)]
+    res, ratios, pooled = {}, [], ([], [])
+    l0 = gz.kernel_launches()
+    t0 = time.perf_counter()
+    for name in names:
+        a = gz.pattern_named(name)
+        model = gz.Plan(a).info()["order"]
+        times = gz.schedule_times(a, G, whole, orientation=True, cutoff=args.cutoff)
+        kept = [t for t in times if t["ms"] >= 0]
+        counts = {gz.count(gz.Plan(a, t["order"]), G, True) for t in kept}
+        if len(counts) != 1:
+            raise SystemExit(f"{name}: schedules disagree on the count: {sorted(counts)}")
+        best = min(kept, key=lambda t: t["ms"])
+        mt = next((t for t in times if t["order"] == model), None)
+        if mt is None:
+            raise SystemExit(f"{name}: the model's schedule {model} is not among Algorithm 4's")
+        by_ms = sorted(kept, key=lambda t: t["ms"])
+        rank_model = next((i + 1 for i, t in enumerate(by_ms) if t["order"] == model), None)
+        r = {"schedules": len(times), "dropped": len(times) - len(kept), "count": counts.pop(),
+             "model_order": model, "model_ms": round(mt["ms"], 3) if mt["ms"] >= 0 else None,
+             "model_rank": rank_model, "best_order": best["order"], "best_ms": round(best["ms"], 3),
+             "spearman_cost_vs_ms": _spearman([t["est_cost"] for t in kept], [t["ms"] for t in kept]),
+             "r2_loglog_cost_vs_ms": _r2_loglog([t["est_cost"] for t in kept], [t["ms"] for t in kept])}
+        # a dropped model schedule took at least cutoff x the best
+        r["model_over_best"] = round((mt["ms"] if mt["ms"] >= 0 else args.cutoff * best["ms"]) / best["ms"], 3)
+        ratios.append(r["model_over_best"])
+        if len(kept) > 1:
+            pooled[0].extend(t["est_cost"] for t in kept)
+            pooled[1].extend(t["ms"] for t in kept)
+        res[name] = r
+    wall = time.perf_counter() - t0
+    launches = gz.kernel_launches() - l0
+    gm = float(np.exp(np.mean(np.log(ratios))))
+    return _line("model-picked schedule time / fastest measured schedule (geometric mean)", gm, "x",
+                 args, world, 1e3 * wall,
+                 {"workload": f"every distinct schedule of {len(names)} patterns, whole-graph counts on "
+                              f"R-MAT scale {scale} ef 16 seed {scale}, oriented; cutoff {args.cutoff}x"},
+                 hib=False, patterns=res, gpu_launches=launches,
+                 pooled_r2_loglog_cost_vs_ms=_r2_loglog(*pooled),
+                 pooled_points=len(pooled[0]),
+                 paper_context="Fig. 11: estimated against actual time, R^2 = 0.94 on Patents")
+
+
 EXTRA = {"triangle": run_triangle, "patterns": run_patterns, "batched": run_batched,
-         "served": run_served, "motifs": run_motifs}
+         "served": run_served, "motifs": run_motifs, "schedules": run_schedules}
 
 
 def main(argv=None):
@@ -666,13 +732,14 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gz", choices=["gz", "reference"])
     ap.add_argument("--config", default="clique",
-                    choices=["clique", "triangle", "patterns", "batched", "served", "motifs"])
+                    choices=["clique", "triangle", "patterns", "batched", "served", "motifs",
+                             "schedules"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scale", type=int, default=0, help="R-MAT scale override (smaller cases)")
     ap.add_argument("--patterns", default="", help="patterns config: comma-separated subset")
-    ap.add_argument("--measured", action="store_true",
-                    help="patterns config: also select each pattern's schedule by timing (NEXT f3)")
+    ap.add_argument("--cutoff", type=float, default=8.0,
+                    help="schedules config: drop a schedule past this multiple of the best time")
     ap.add_argument("--full", default="", help="patterns config: patterns whose full count is timed "
                     "(default none at scale 22, all below)")
     ap.add_argument("--requests", type=int, default=300, help="served config: requests per rate")

@@ -146,15 +146,35 @@ gz_status gz_plan_info(const gz_plan* p, int* k, int32_t* order, int32_t* bound_
 gz_status gz_plan_schedules(int k, const uint8_t* adj, int32_t* orders, int cap, int* count);
 
 /*
- * Measured schedule selection: the Sec. 5.4 performance model ranks schedules
- * on a uniform random graph (n = 1000, degree 5); this instead times every
- * distinct schedule (Algorithm 4) on the given graph, counting the roots of the
- * nsample ranges [sample_lo[i], sample_hi[i]) (ids of the view counted), and
- * plans the fastest (first on ties). A schedule whose running time passes 4x
- * the best total so far is dropped between ranges. The count does not depend
- * on the schedule, only the time does. *best_ms (optional) receives the chosen
- * schedule's time on the samples, *model_ms (optional) that of the schedule
- * gz_plan_create would pick. Errors: as gz_plan_create and gz_count_ex.
+ * Measured schedule times, the measured side of the Sec. 5.4 performance model
+ * (whose estimates against measured times are Fig. 11): for every distinct
+ * schedule of the pattern (Algorithm 4, generation order, k labels each into
+ * orders) writes the model's estimated cost (est_cost, as gz_plan_info) and the
+ * host wall time in ms of counting the roots of the nsample ranges
+ * [sample_lo[i], sample_hi[i]) with it (ms; one synchronous gz_count_ex per
+ * range, summed). The first schedule is run once untimed first, to build the
+ * views and scratch. With cutoff > 0 a schedule is dropped (ms = -1) once its
+ * total passes cutoff x the best complete total so far; cutoff <= 0 times every
+ * schedule in full. The root of a schedule is its first pattern vertex, so a
+ * range holds a different share of the total work under each schedule:
+ * [0, n) compares whole counts; otherwise use ranges spread over the id range.
+ * With orders, est_cost and ms all NULL only *count is written. Errors:
+ * GZ_EINVAL (bad pattern, graph or ranges; cap below the count), and those of
+ * gz_count_ex.
+ */
+gz_status gz_schedule_times(int k, const uint8_t* adj, const gz_graph* g, int use_orientation,
+                            const int64_t* sample_lo, const int64_t* sample_hi, int nsample,
+                            void* stream, double cutoff, int32_t* orders, double* est_cost,
+                            double* ms, int cap, int* count);
+
+/*
+ * Measured schedule selection: plans the schedule with the smallest time in
+ * gz_schedule_times (cutoff 4; first on ties) instead of the one the Sec. 5.4
+ * model ranks first on a uniform random graph (n = 1000, degree 5). The count
+ * does not depend on the schedule, only the time does. *best_ms (optional)
+ * receives the chosen schedule's time on the samples, *model_ms (optional)
+ * that of the schedule gz_plan_create picks, or -1 if that one was dropped at
+ * 4x the best. Errors: as gz_schedule_times.
  */
 gz_status gz_plan_create_measured(int k, const uint8_t* adj, const gz_graph* g,
                                   int use_orientation, const int64_t* sample_lo,

@@ -29,7 +29,7 @@ EXPORTS = [
     "gz_plan_schedules", "gz_plan_describe", "gz_plan_destroy", "gz_count", "gz_count_ex", "gz_scratch_bytes",
     "gz_count_batch", "gz_count_noalloc", "gz_autotune", "gz_server_create", "gz_server_submit", "gz_server_wait",
     "gz_server_replay", "gz_server_destroy", "gz_last_error", "gz_version", "gz_kernel_launches",
-    "gz_motif_patterns", "gz_count_motifs", "gz_plan_create_measured",
+    "gz_motif_patterns", "gz_count_motifs", "gz_plan_create_measured", "gz_schedule_times",
 ]
 
 
@@ -97,6 +97,9 @@ def lib() -> ctypes.CDLL:
         "gz_motif_patterns": [I, _u8p, I, ctypes.POINTER(I)],
         "gz_plan_create_measured": [I, _u8p, _P, I, _i64p, _i64p, I, _P, ctypes.POINTER(_P),
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+        "gz_schedule_times": [I, _u8p, _P, I, _i64p, _i64p, I, _P, ctypes.c_double, _i32p,
+                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), I,
+                              ctypes.POINTER(I)],
         "gz_count_motifs": [_P, I, I, _P, _u64p, I, ctypes.POINTER(I)],
         "gz_server_create": [ctypes.POINTER(ServerOpts), ctypes.POINTER(_P)],
         "gz_server_submit": [_P, _P, _P, I, _i64p],
@@ -205,12 +208,39 @@ class Plan:
             pass
 
 
+def _ranges(samples):
+    lo = np.ascontiguousarray([s[0] for s in samples], dtype=np.int64)
+    hi = np.ascontiguousarray([s[1] for s in samples], dtype=np.int64)
+    return lo, hi
+
+
+def schedule_times(adj, graph: "Graph", samples, orientation: bool = True, cutoff: float = 0.0,
+                   stream=None) -> list:
+    """Every distinct schedule timed on the root ranges samples = [(lo, hi), ...]:
+    a list of {"order", "est_cost", "ms"} in Algorithm 4's order (ms = -1: dropped
+    past cutoff x the best)."""
+    a, k = _adj(adj)
+    lo, hi = _ranges(samples)
+    cnt = ctypes.c_int()
+    args = (k, a.ctypes.data_as(_u8p), graph.handle, int(orientation), lo.ctypes.data_as(_i64p),
+            hi.ctypes.data_as(_i64p), len(samples), _stream(stream), float(cutoff))
+    _check(lib().gz_schedule_times(*args, None, None, None, 0, ctypes.byref(cnt)), "gz_schedule_times")
+    n = cnt.value
+    orders = np.zeros((max(n, 1), k), dtype=np.int32)
+    cost = np.zeros(max(n, 1))
+    ms = np.zeros(max(n, 1))
+    _dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib().gz_schedule_times(*args, orders.ctypes.data_as(_i32p), cost.ctypes.data_as(_dp),
+                                   ms.ctypes.data_as(_dp), n, ctypes.byref(cnt)), "gz_schedule_times")
+    return [{"order": orders[i].tolist(), "est_cost": float(cost[i]), "ms": float(ms[i])}
+            for i in range(n)]
+
+
 def plan_measured(adj, graph: "Graph", samples, orientation: bool = True, stream=None):
     """The fastest distinct schedule of the pattern on graph, timed on the root
     ranges samples = [(lo, hi), ...]; returns (Plan, best_ms, model_ms)."""
     a, k = _adj(adj)
-    lo = np.ascontiguousarray([s[0] for s in samples], dtype=np.int64)
-    hi = np.ascontiguousarray([s[1] for s in samples], dtype=np.int64)
+    lo, hi = _ranges(samples)
     h = _P()
     best, model = ctypes.c_double(), ctypes.c_double()
     _check(lib().gz_plan_create_measured(k, a.ctypes.data_as(_u8p), graph.handle, int(orientation),

@@ -530,25 +530,30 @@ gz_status gz_plan_info(const gz_plan* p, int* k, int32_t* order, int32_t* bound_
     return GZ_OK;
 }
 
-gz_status gz_plan_create_measured(int k, const uint8_t* adj, const gz_graph* g,
-                                  int use_orientation, const int64_t* sample_lo,
-                                  const int64_t* sample_hi, int nsample, void* stream,
-                                  gz_plan** out, double* best_ms, double* model_ms) {
-    GZ_RANGE("gz_plan_create_measured");
-    if (!out || !check_graph(g, "gz_plan_create_measured") || nsample < 1 || !sample_lo || !sample_hi) {
-        set_error("gz_plan_create_measured: bad arguments");
+gz_status gz_schedule_times(int k, const uint8_t* adj, const gz_graph* g, int use_orientation,
+                            const int64_t* sample_lo, const int64_t* sample_hi, int nsample,
+                            void* stream, double cutoff, int32_t* orders, double* est_cost,
+                            double* ms, int cap, int* count) {
+    GZ_RANGE("gz_schedule_times");
+    if (!count || !check_graph(g, "gz_schedule_times") || nsample < 1 || !sample_lo || !sample_hi) {
+        set_error("gz_schedule_times: bad arguments");
         return GZ_EINVAL;
     }
-    *out = nullptr;
     int ns = 0;
     gz_status st = list_schedules(k, adj, nullptr, 0, &ns);
     if (st != GZ_OK) return st;
-    std::vector<int32_t> orders((size_t)ns * k);
-    list_schedules(k, adj, orders.data(), ns, &ns);
-    gz_plan* model = nullptr;
-    st = make_plan(k, adj, nullptr, &model);
-    if (st != GZ_OK) return st;
-    auto time_plan = [&](const gz_plan* p, double cutoff, double* ms) -> gz_status {
+    *count = ns;
+    if (cap < ns || !orders || !est_cost || !ms) {
+        if (orders || est_cost || ms) {
+            set_error("gz_schedule_times: %d schedules, room for %d", ns, cap);
+            return GZ_EINVAL;
+        }
+        return GZ_OK;
+    }
+    list_schedules(k, adj, orders, ns, &ns);
+    // sum over the sample ranges of one synchronous count each; stops early once
+    // the total passes limit (then returns a total above limit)
+    auto time_plan = [&](const gz_plan* p, double limit, double* out_ms) -> gz_status {
         double total = 0.0;
         for (int i = 0; i < nsample; ++i) {
             gz_count_opts o{};
@@ -557,46 +562,64 @@ gz_status gz_plan_create_measured(int k, const uint8_t* adj, const gz_graph* g,
             o.root_hi = sample_hi[i];
             uint64_t c = 0;
             const auto t0 = std::chrono::steady_clock::now();
-            gz_status r = gz_count_ex(p, g, &o, stream, &c);  // synchronous
+            gz_status r = gz_count_ex(p, g, &o, stream, &c);
             if (r != GZ_OK) return r;
             total += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-            if (total > cutoff) break;
+            if (total > limit) break;
         }
-        *ms = total;
+        *out_ms = total;
         return GZ_OK;
     };
-    // warm the views the plans need, then time the model's choice first
-    double mms = 0.0;
-    st = time_plan(model, 1e300, &mms);
-    if (st == GZ_OK) st = time_plan(model, 1e300, &mms);
-    double best = mms;
-    int besti = -1;  // -1: the model's plan
+    double best = 1e300;
     for (int i = 0; i < ns && st == GZ_OK; ++i) {
-        if (memcmp(orders.data() + (size_t)i * k, model->order, sizeof(int32_t) * k) == 0) continue;
         gz_plan* p = nullptr;
-        st = make_plan(k, adj, orders.data() + (size_t)i * k, &p);
+        st = make_plan(k, adj, orders + (size_t)i * k, &p);
         if (st != GZ_OK) break;
-        double ms = 0.0;
-        st = time_plan(p, 4.0 * best, &ms);
+        est_cost[i] = p->est_cost;
+        double t = 0.0;
+        if (i == 0) st = time_plan(p, 1e300, &t);  // warm-up: views, scratch, caches
+        const double limit = cutoff > 0.0 && best < 1e300 ? cutoff * best : 1e300;
+        if (st == GZ_OK) st = time_plan(p, limit, &t);
         gz_plan_destroy(p);
-        if (st == GZ_OK && ms < best) {
-            best = ms;
-            besti = i;
-        }
+        if (st != GZ_OK) break;
+        ms[i] = t > limit ? -1.0 : t;
+        if (t <= limit && t < best) best = t;
     }
-    if (st != GZ_OK) {
-        gz_plan_destroy(model);
-        return st;
+    return st;
+}
+
+gz_status gz_plan_create_measured(int k, const uint8_t* adj, const gz_graph* g,
+                                  int use_orientation, const int64_t* sample_lo,
+                                  const int64_t* sample_hi, int nsample, void* stream,
+                                  gz_plan** out, double* best_ms, double* model_ms) {
+    GZ_RANGE("gz_plan_create_measured");
+    if (!out) {
+        set_error("gz_plan_create_measured: out is NULL");
+        return GZ_EINVAL;
     }
-    if (besti < 0) {
-        *out = model;
-    } else {
-        gz_plan_destroy(model);
-        st = make_plan(k, adj, orders.data() + (size_t)besti * k, out);
-        if (st != GZ_OK) return st;
+    *out = nullptr;
+    int ns = 0;
+    gz_status st = gz_schedule_times(k, adj, g, use_orientation, sample_lo, sample_hi, nsample,
+                                     stream, 0.0, nullptr, nullptr, nullptr, 0, &ns);
+    if (st != GZ_OK) return st;
+    std::vector<int32_t> orders((size_t)ns * k);
+    std::vector<double> cost(ns), ms(ns);
+    st = gz_schedule_times(k, adj, g, use_orientation, sample_lo, sample_hi, nsample, stream, 4.0,
+                           orders.data(), cost.data(), ms.data(), ns, &ns);
+    if (st != GZ_OK) return st;
+    gz_plan* model = nullptr;
+    st = make_plan(k, adj, nullptr, &model);
+    if (st != GZ_OK) return st;
+    int besti = -1, modeli = -1;
+    for (int i = 0; i < ns; ++i) {
+        if (memcmp(orders.data() + (size_t)i * k, model->order, sizeof(int32_t) * k) == 0) modeli = i;
+        if (ms[i] >= 0.0 && (besti < 0 || ms[i] < ms[besti])) besti = i;
     }
-    if (best_ms) *best_ms = best;
-    if (model_ms) *model_ms = mms;
+    gz_plan_destroy(model);
+    st = make_plan(k, adj, orders.data() + (size_t)besti * k, out);
+    if (st != GZ_OK) return st;
+    if (best_ms) *best_ms = ms[besti];
+    if (model_ms) *model_ms = modeli >= 0 ? ms[modeli] : -1.0;
     return GZ_OK;
 }
 
