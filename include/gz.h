@@ -286,13 +286,14 @@ gz_status gz_autotune(const gz_plan* p, const gz_graph* g, int use_orientation, 
 
 /* ------------------------------------------------------------------ motifs */
 
-#define GZ_MOTIF_MAX_K 6
+#define GZ_MOTIF_MAX_K 7
 
 /*
  * Motif patterns (the workload of the paper's Table 2, Sec. 7.1-7.2): every
  * connected graph on k vertices (2 <= k <= GZ_MOTIF_MAX_K) up to isomorphism,
- * ordered by edge count and then by canonical code; 1, 2, 6, 21 and 112 patterns
- * for k = 2..6 (Sec. 7.2 quotes 2 on 3 vertices and 21 on 5; Sec. 1, 112 of size 6). Writes up to cap
+ * ordered by edge count and then by canonical code; 1, 2, 6, 21, 112 and 853
+ * patterns for k = 2..7 (Sec. 7.2 quotes 2 on 3 vertices and 21 on 5; Sec. 1,
+ * 112 of size 6 and 853 of size 7). Writes up to cap
  * patterns as k*k uint8 adjacencies (row-major, consecutive) to adjs (may be
  * NULL) and the number of patterns to *count. Errors: GZ_EINVAL (k out of range).
  */

@@ -1,6 +1,6 @@
 // gz_motif.cpp - motif counting: the counts of every connected k-vertex pattern
 // (Sec. 7.1-7.2 count the motifs of 3 to 5 vertices: 2 patterns on 3 vertices,
-// 21 on 5; Sec. 1 quotes 112 size-6 patterns). The patterns are enumerated on the
+// 21 on 5; Sec. 1 quotes 112 size-6 and 853 size-7 patterns). The patterns are enumerated on the
 // host, each is planned like any other pattern, and all of them are counted in
 // one batched call.
 #include <algorithm>
@@ -23,46 +23,52 @@ inline int ebit(int i, int j, int k) {
     return b + (j - i - 1);
 }
 
-bool connected(int k, uint32_t edges) {
-    uint32_t seen = 1, frontier = 1;
-    while (frontier) {
-        uint32_t next = 0;
-        for (int v = 0; v < k; ++v) {
-            if (!(frontier >> v & 1)) continue;
-            for (int u = 0; u < k; ++u)
-                if (u != v && (edges >> ebit(std::min(u, v), std::max(u, v), k) & 1) && !(seen >> u & 1))
-                    next |= 1u << u;
-        }
-        seen |= next;
-        frontier = next;
-    }
-    return seen == (1u << k) - 1;
-}
-
 // Canonical code of an edge set: the smallest edge bitmask over the relabellings
-// that list the vertices by decreasing degree (an isomorphism maps each degree
-// class onto itself, so the minimum over these is the same for the whole
-// class); the classes are permuted independently, odometer style.
+// that list the vertices by colour, where the colours come from refining the
+// degrees (a vertex's new colour ranks its colour together with the sorted
+// colours of its neighbours) until the number of colours stops growing. The
+// refinement commutes with relabelling, so an isomorphism maps each colour class
+// onto itself and the minimum over the permutations inside the classes is the
+// same for every graph of an isomorphism class; the classes are permuted
+// independently, odometer style.
 uint32_t canonical(int k, uint32_t edges) {
-    int deg[GZ_MAX_K] = {0};
+    bool adj[GZ_MAX_K][GZ_MAX_K] = {};
+    int color[GZ_MAX_K] = {0};
     for (int i = 0; i < k; ++i)
         for (int j = i + 1; j < k; ++j)
-            if (edges >> ebit(i, j, k) & 1) { ++deg[i]; ++deg[j]; }
+            if (edges >> ebit(i, j, k) & 1) { adj[i][j] = adj[j][i] = true; ++color[i]; ++color[j]; }
+    int ncolors = 0;
+    for (;;) {
+        std::vector<std::vector<int>> sig(k);
+        for (int v = 0; v < k; ++v) {
+            sig[v].push_back(color[v]);
+            std::vector<int> nb;
+            for (int u = 0; u < k; ++u)
+                if (adj[v][u]) nb.push_back(color[u]);
+            std::sort(nb.begin(), nb.end());
+            sig[v].insert(sig[v].end(), nb.begin(), nb.end());
+        }
+        std::vector<std::vector<int>> dist(sig);
+        std::sort(dist.begin(), dist.end());
+        dist.erase(std::unique(dist.begin(), dist.end()), dist.end());
+        for (int v = 0; v < k; ++v)
+            color[v] = (int)(std::lower_bound(dist.begin(), dist.end(), sig[v]) - dist.begin());
+        if ((int)dist.size() == ncolors) break;
+        ncolors = (int)dist.size();
+    }
     int perm[GZ_MAX_K];
     for (int i = 0; i < k; ++i) perm[i] = i;
-    std::sort(perm, perm + k, [&](int a, int b) { return deg[a] != deg[b] ? deg[a] > deg[b] : a < b; });
+    std::sort(perm, perm + k, [&](int a, int b) { return color[a] != color[b] ? color[a] < color[b] : a < b; });
     int start[GZ_MAX_K + 1], ng = 0;  // class boundaries in perm
     for (int i = 0; i < k; ++i)
-        if (i == 0 || deg[perm[i]] != deg[perm[i - 1]]) start[ng++] = i;
+        if (i == 0 || color[perm[i]] != color[perm[i - 1]]) start[ng++] = i;
     start[ng] = k;
     uint32_t best = UINT32_MAX;
     for (;;) {
         uint32_t code = 0;
         for (int i = 0; i < k; ++i)
-            for (int j = i + 1; j < k; ++j) {
-                const int a = std::min(perm[i], perm[j]), b = std::max(perm[i], perm[j]);
-                if (edges >> ebit(a, b, k) & 1) code |= 1u << ebit(i, j, k);
-            }
+            for (int j = i + 1; j < k; ++j)
+                if (adj[perm[i]][perm[j]]) code |= 1u << ebit(i, j, k);
         best = std::min(best, code);
         int g = ng - 1;  // advance the last class; on wrap-around carry into the previous one
         while (g >= 0 && !std::next_permutation(perm + start[g], perm + start[g + 1])) --g;
@@ -73,16 +79,27 @@ uint32_t canonical(int k, uint32_t edges) {
 
 }  // namespace
 
+const std::vector<uint32_t>& motif_codes(int k);
+
 // Every connected graph on k labelled vertices up to isomorphism, as canonical
-// edge sets, ordered by edge count and then by code.
+// edge sets, ordered by edge count and then by code. Removing a leaf of a
+// spanning tree leaves a connected graph connected, so every k-vertex one is a
+// connected (k-1)-vertex graph plus a vertex joined to a non-empty subset of it.
 std::vector<uint32_t> motif_codes_uncached(int k) {
-    const int ne = k * (k - 1) / 2;
+    if (k == 2) return {1u};
     std::set<std::pair<int, uint32_t>> found;
-    std::set<uint32_t> seen;
-    for (uint32_t e = 0; e < (1u << ne); ++e) {
-        if (__builtin_popcount(e) < k - 1 || !connected(k, e)) continue;
-        const uint32_t c = canonical(k, e);
-        if (seen.insert(c).second) found.insert({__builtin_popcount(c), c});
+    for (const uint32_t c : motif_codes(k - 1)) {
+        uint32_t base = 0;
+        for (int i = 0; i < k - 1; ++i)
+            for (int j = i + 1; j < k - 1; ++j)
+                if (c >> ebit(i, j, k - 1) & 1) base |= 1u << ebit(i, j, k);
+        for (uint32_t sub = 1; sub < (1u << (k - 1)); ++sub) {
+            uint32_t e = base;
+            for (int i = 0; i < k - 1; ++i)
+                if (sub >> i & 1) e |= 1u << ebit(i, k - 1, k);
+            const uint32_t cc = canonical(k, e);
+            found.insert({__builtin_popcount(cc), cc});
+        }
     }
     std::vector<uint32_t> out;
     for (const auto& f : found) out.push_back(f.second);
@@ -91,10 +108,10 @@ std::vector<uint32_t> motif_codes_uncached(int k) {
 
 // The same, computed once per k and process.
 const std::vector<uint32_t>& motif_codes(int k) {
-    static std::mutex mu;
+    static std::recursive_mutex mu;  // the k list is built from the k-1 list
     static std::vector<uint32_t> cache[GZ_MOTIF_MAX_K + 1];
     static bool done[GZ_MOTIF_MAX_K + 1] = {};
-    std::lock_guard<std::mutex> lk(mu);
+    std::lock_guard<std::recursive_mutex> lk(mu);
     if (!done[k]) {
         cache[k] = motif_codes_uncached(k);
         done[k] = true;

@@ -426,3 +426,39 @@ def test_schedule_times_every_schedule():
     for t in times[:3]:
         p = gz.Plan(a, t["order"])
         assert gz.count(p, G, True, 0, 300) + gz.count(p, G, True, 300, g.n) == want
+
+
+def _first_connected_order(a):
+    """A valid schedule for the oracle: each vertex after the first is adjacent
+    to an earlier one (the count does not depend on which valid schedule runs)."""
+    k = len(a)
+    order = [0]
+    while len(order) < k:
+        order.append(next(v for v in range(k) if v not in order and any(a[v][u] for u in order)))
+    return order
+
+
+def test_count_motifs_size7():
+    """All 853 connected 7-vertex patterns (Sec. 1) counted in one batch: each count
+    equals the oracle's, and on the 14-vertex graph they add up to the number of
+    connected induced 7-vertex subgraphs, found by brute force."""
+    import itertools
+    pats = gz.motif_patterns(7)
+    for g in [S.random_small(14, 0.35, 61), S.random_small(40, 0.15, 72)]:
+        G = gz.Graph.from_csr(g).orient()
+        got = gz.count_motifs(G, 7, orientation=True)
+        go, _ = O.reindex(g)
+        assert got == [O.count_nested(a, _first_connected_order(a), go)[0] for a in pats]
+        if g.n <= 14:
+            nb = [set(g.neighbors(v).tolist()) for v in range(g.n)]
+            conn = 0
+            for sub in itertools.combinations(range(g.n), 7):
+                seen, todo = {sub[0]}, [sub[0]]
+                while todo:
+                    v = todo.pop()
+                    for u in sub:
+                        if u not in seen and u in nb[v]:
+                            seen.add(u)
+                            todo.append(u)
+                conn += len(seen) == 7
+            assert sum(got) == conn

@@ -266,3 +266,39 @@ def test_motif_patterns_match_oracle(k):
     mine = [O.canonical_form(a) for a in gz.motif_patterns(k)]
     assert len(mine) == len(set(mine))
     assert set(mine) == {O.canonical_form(a) for a in O.connected_patterns(k)}
+
+
+def _connected(a) -> bool:
+    k = len(a)
+    seen, todo = {0}, [0]
+    while todo:
+        v = todo.pop()
+        for u in range(k):
+            if a[v][u] and u not in seen:
+                seen.add(u)
+                todo.append(u)
+    return len(seen) == k
+
+
+def test_motif_patterns_size7():
+    """Sec. 1 puts the number of connected 7-vertex patterns at 853. The library's
+    list has that many, each connected, no two isomorphic (the oracle's canonical
+    form over all 7! relabellings), so it holds every class exactly once."""
+    pats = gz.motif_patterns(7)
+    assert len(pats) == 853
+    for a in pats:
+        assert (a == a.T).all() and not a.diagonal().any() and _connected(a)
+    forms = {O.canonical_form(a) for a in pats}
+    assert len(forms) == 853
+
+
+def test_plan_every_size7_motif():
+    """Every 7-vertex motif plans (Algorithm 4 schedules, Algorithm 1 + Theorem 2
+    restrictions, Sec. 5.4 model) with a valid schedule and |Aut(P)| matching the
+    oracle's."""
+    pats = gz.motif_patterns(7)
+    for idx, a in enumerate(pats):
+        info = gz.Plan(a).info()
+        assert sorted(info["order"]) == list(range(7))
+        if idx % 40 == 0:
+            assert info["aut_size"] == len(O.automorphisms(a))
