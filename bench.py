@@ -721,8 +721,47 @@ def run_schedules(args, dist, world, rank, local):
                  paper_context="Fig. 11: estimated against actual time, R^2 = 0.94 on Patents")
 
 
+def run_planner(args, dist, world, rank, local):
+    """Planner throughput on the host (Algorithm 4 schedules, Algorithm 1 +
+    Theorem 2 restrictions, Sec. 5.4 model, program compile): every connected
+    7-vertex pattern (853, Sec. 1) planned once per step, and K7 minus one edge
+    (the Sec. 7.3 example). No GPU work."""
+    import paper_1911_12877_gb300 as gz
+    pats = gz.motif_patterns(7)
+    for _ in range(args.warmup):
+        for a in pats[:50]:
+            gz.Plan(a)
+    steps, worst = [], (0.0, None)
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for i, a in enumerate(pats):
+            t = time.perf_counter()
+            gz.Plan(a)
+            dt = time.perf_counter() - t
+            if dt > worst[0]:
+                worst = (dt, i)
+        steps.append(time.perf_counter() - t0)
+    k7e = []
+    for _ in range(max(args.steps, 5)):
+        t = time.perf_counter()
+        gz.Plan("chordal7")
+        k7e.append(time.perf_counter() - t)
+    ms = 1e3 * statistics.median(steps)
+    wa = pats[worst[1]]
+    return _line("plan all 853 connected 7-vertex patterns", ms, "ms", args, world, ms,
+                 {"workload": "host planner over every connected 7-vertex pattern, one thread"},
+                 hib=False, gpu_launches=0,
+                 max_pattern_ms=round(1e3 * worst[0], 3),
+                 max_pattern_edges=int(wa.sum()) // 2,
+                 max_pattern_schedules=len(gz.schedules(wa)),
+                 k7_minus_edge_ms=round(1e3 * statistics.median(k7e), 3),
+                 paper_context="Sec. 7.3: 853-pattern motif-7 compile 37 s; the hardest 7-vertex "
+                               "patterns under 30 ms each; K7 minus one edge 0.6 ms (2x8 Xeon cores)")
+
+
 EXTRA = {"triangle": run_triangle, "patterns": run_patterns, "batched": run_batched,
-         "served": run_served, "motifs": run_motifs, "schedules": run_schedules}
+         "served": run_served, "motifs": run_motifs, "schedules": run_schedules,
+         "planner": run_planner}
 
 
 def main(argv=None):
@@ -733,7 +772,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="gz", choices=["gz", "reference"])
     ap.add_argument("--config", default="clique",
                     choices=["clique", "triangle", "patterns", "batched", "served", "motifs",
-                             "schedules"])
+                             "schedules", "planner"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scale", type=int, default=0, help="R-MAT scale override (smaller cases)")
