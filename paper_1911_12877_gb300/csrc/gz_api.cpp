@@ -545,7 +545,7 @@ gz_status gz_schedule_times(int k, const uint8_t* adj, const gz_graph* g, int us
     *count = ns;
     if (cap < ns || !orders || !est_cost || !ms) {
         if (orders || est_cost || ms) {
-            set_error("gz_schedule_times: %d schedules, room for %d", ns, cap);
+            set_error("gz_schedule_times: orders, est_cost and ms need room for %d schedules (cap %d)", ns, cap);
             return GZ_EINVAL;
         }
         return GZ_OK;

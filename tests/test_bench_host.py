@@ -1,0 +1,43 @@
+"""Host-only parts of bench.py: the statistics of the schedules config and the
+planner config's JSON line (the planner runs on the CPU)."""
+import json
+
+import numpy as np
+import pytest
+
+import bench
+
+
+def test_r2_loglog_exact_power_law():
+    x = np.array([1.0, 2.0, 5.0, 10.0, 40.0])
+    assert bench._r2_loglog(x, 3.0 * x ** 1.7) == pytest.approx(1.0)
+    assert bench._r2_loglog([1, 2], [3, 4]) is None  # fewer than 3 points
+    assert bench._r2_loglog([1, 1, 1], [1, 2, 3]) is None  # no spread
+
+
+def test_r2_loglog_matches_least_squares():
+    rng = np.random.default_rng(3)
+    x = np.exp(rng.normal(size=30))
+    y = np.exp(0.5 * np.log(x) + rng.normal(scale=0.5, size=30))
+    lx, ly = np.log(x), np.log(y)
+    a, b = np.polyfit(lx, ly, 1)
+    resid = ly - (a * lx + b)
+    r2 = 1 - (resid ** 2).sum() / ((ly - ly.mean()) ** 2).sum()
+    assert bench._r2_loglog(x, y) == pytest.approx(r2)
+
+
+def test_spearman():
+    assert bench._spearman([1, 2, 3, 4], [10, 20, 30, 40]) == pytest.approx(1.0)
+    assert bench._spearman([1, 2, 3, 4], [9, 7, 5, 1]) == pytest.approx(-1.0)
+    assert bench._spearman([1, 2], [2, 1]) is None
+
+
+def test_planner_config_line(capsys):
+    pytest.importorskip("paper_1911_12877_gb300")
+    assert bench.main(["--config", "planner", "--steps", "1", "--warmup", "3"]) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "config", "gpu_launches"):
+        assert key in line
+    assert line["gpu_launches"] == 0 and line["unit"] == "ms" and line["value"] > 0
+    assert line["max_pattern_schedules"] >= 1
