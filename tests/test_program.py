@@ -302,3 +302,29 @@ def test_plan_every_size7_motif():
         assert sorted(info["order"]) == list(range(7))
         if idx % 40 == 0:
             assert info["aut_size"] == len(O.automorphisms(a))
+
+
+def test_size7_motifs_planner_and_program_match_oracle():
+    """A spread sample of the 853 size-7 motifs: the library's plan equals the
+    oracle planner's (schedule, Theorem 2 bound parents, |Aut(P)|, Sec. 5.4 cost),
+    and its compiled program, interpreted with the kernels' operand rules, counts
+    what brute force over all 7-subsets counts (Sec. 2.1 definition)."""
+    pats = gz.motif_patterns(7)
+    # sparse, medium and dense, so that most sampled patterns occur in one of them
+    graphs = [S.random_small(13, 0.3, 31), S.random_small(13, 0.5, 32), S.random_small(13, 0.7, 33)]
+    for idx in range(0, len(pats), 17):
+        a = pats[idx]
+        info = gz.Plan(a).info()
+        order, cost = O.choose_schedule(a)
+        bp, _ = O.restrictions(a, order)
+        assert info["order"] == list(order), idx
+        assert info["bound_parent"] == list(bp), idx
+        assert info["aut_size"] == len(O.automorphisms(a)), idx
+        assert info["est_cost"] == pytest.approx(cost, rel=1e-12), idx
+        prog = parse(gz.Plan(a).describe())
+        for g in graphs:
+            want = O.count_brute_induced(a, g)
+            go, _ = O.reindex(g)
+            for flat in (False, True):
+                assert Interp(prog, 7, g, flat, None).run() == want, (idx, flat)
+                assert Interp(prog, 7, go, flat, None).run() == want, (idx, flat, "oriented")
