@@ -249,8 +249,8 @@ def _golden(name):
 
 def test_clique_rmat20_full_and_sampled():
     """k-clique workload (R-MAT scale 20, ef 16, seed 20, oriented), in the launch
-    configuration the bench times: K4 in full against the stored oracle count, K5 on
-    sampled root ranges against the oracle computed here."""
+    configuration the bench times: K4 and K5 in full, and K5 on sampled root ranges,
+    against the stored oracle counts."""
     gold = _golden("clique_rmat20.json")
     g = S.rmat_clique()
     assert g.nnz == gold["nnz"]
