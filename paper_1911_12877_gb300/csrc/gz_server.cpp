@@ -115,7 +115,10 @@ gz_status launch_batch(gz_server* s, Slot& sl) {
     unsigned long long* d = nullptr;
     cudaError_t e = cudaMallocAsync(&scratch, need, sl.stream);
     if (e == cudaSuccess) e = cudaMallocAsync(&d, sizeof(unsigned long long) * words, sl.stream);
-    if (e != cudaSuccess) return cuda_fail(e, "server: scratch");
+    if (e != cudaSuccess) {
+        if (scratch) cudaFreeAsync(scratch, sl.stream);
+        return cuda_fail(e, "server: scratch");
+    }
     e = cudaMemsetAsync(d, 0, sizeof(unsigned long long) * words, sl.stream);
     gz_status st = e == cudaSuccess ? GZ_OK : cuda_fail(e, "server: memset");
     if (st == GZ_OK)
