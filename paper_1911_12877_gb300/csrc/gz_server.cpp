@@ -329,9 +329,10 @@ gz_status gz_server_replay(gz_server* s, const gz_plan* const* plans, const gz_g
         set_error("gz_server_replay: bad arguments");
         return GZ_EINVAL;
     }
-    const int64_t launches0 = s->launches;
+    int64_t launches0;
     {
         std::lock_guard<std::mutex> lk(s->mu);
+        launches0 = s->launches;
         s->max_queue = 0;
     }
     std::vector<int64_t> tickets(nreq, 0);
@@ -373,6 +374,7 @@ gz_status gz_server_replay(gz_server* s, const gz_plan* const* plans, const gz_g
     }
     double wall = std::chrono::duration<double>(Clock::now() - t0).count();
     if (stats_out) {
+        std::lock_guard<std::mutex> lk(s->mu);  // the worker updates both counters
         stats_out[0] = wall > 0 ? (double)nreq / wall : 0.0;
         stats_out[1] = (double)s->max_queue;
         stats_out[2] = (double)(s->launches - launches0);
