@@ -233,25 +233,32 @@ gz_status gz_count_ex(const gz_plan* p, const gz_graph* g, const gz_count_opts* 
 #define GZ_NOALLOC_SCRATCH_BYTES (32ull << 20)
 
 /*
- * gz_count for callers that cannot allocate device memory when they count:
- * code that runs while a CUDA stream is being captured into a graph, real-time
- * loops that forbid allocator calls after start-up, or hosts whose own memory
- * manager owns the whole device. The paper has no counterpart.
+ * gz_count for callers that cannot allocate device memory when they count. The
+ * paper has no counterpart. Typical callers: real-time or latency-bound loops
+ * whose rules forbid allocator calls once they have started (an allocation can
+ * block on the driver or fail under memory pressure at a bad moment), and host
+ * applications whose own memory manager reserves the whole device up front, so
+ * that a cudaMalloc by a library inside them fails or fragments their pool.
  *
  * Counts the plan's pattern over the whole graph (use_orientation as in
  * gz_count) with the general enumeration kernel and writes the exact count to
  * *out_count (host). It calls no cudaMalloc, cudaFree or other allocating
- * routine: its counters and set-operation scratch live in a static device
- * array of 256 + GZ_NOALLOC_SCRATCH_BYTES bytes that every GPU using the
- * library holds until the process exits; a plan whose per-warp scratch exceeds
- * GZ_NOALLOC_SCRATCH_BYTES gets GZ_EOVERFLOW, and smaller ones run on as many
- * warps as the array holds. The graph's views must already exist: call
- * gz_orient (use_orientation = 1) or one gz_count with this plan first, else
- * GZ_EINVAL. The first call on each device looks up the array's device address
- * (once per device, with that device current); make that first call before any
- * stream capture. Every call shares the array and the call clears its counters
- * itself; calls whose kernels overlap on the GPU race on it, so the caller must
- * serialise them. Synchronous on `stream`.
+ * routine (gz_allocations() does not change): its counters and set-operation
+ * scratch live in a static device array of 256 + GZ_NOALLOC_SCRATCH_BYTES bytes
+ * that every GPU using the library holds until the process exits. A plan whose
+ * per-warp scratch exceeds GZ_NOALLOC_SCRATCH_BYTES gets GZ_EOVERFLOW with a
+ * message naming both sizes; smaller ones run on as many warps as the array
+ * holds. The graph's views must already exist: call gz_orient
+ * (use_orientation = 1) or one gz_count with this plan first, else GZ_EINVAL.
+ *
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and keeps it for later
+ * calls. After cudaDeviceReset on a device that address is stale, so do not
+ * call this entry point on that device again in the same process. Every call
+ * shares the array and clears its counters itself; calls whose kernels overlap
+ * on the GPU (other streams, other host threads) race on it, so the caller
+ * must serialise them. Synchronous on `stream`: the count is read back into
+ * host memory before the call returns.
  */
 gz_status gz_count_noalloc(const gz_plan* p, const gz_graph* g, int use_orientation, void* stream,
                            uint64_t* out_count);
@@ -366,6 +373,13 @@ const char* gz_version(void);
 
 /* Number of CUDA kernels libgz has launched in this process (all streams). */
 uint64_t gz_kernel_launches(void);
+
+/*
+ * Number of memory allocation calls (cudaMalloc, cudaMallocAsync,
+ * cudaMallocHost) libgz has made in this process. Lets a caller check that a
+ * path allocated nothing, e.g. around gz_count_noalloc.
+ */
+uint64_t gz_allocations(void);
 
 #ifdef __cplusplus
 }

@@ -26,6 +26,7 @@ _LIB = os.path.join(_HERE, "libgz_oracle.so")
 MUTATIONS = {
     "none": 0, "drop_red": 1, "no_bound": 2, "no_exclude": 3, "bound_le": 4,
     "alg1_nostab": 5, "thm2_first": 6, "aut_next_only": 7, "reindex_asc": 8, "e_full": 9,
+    "cost_no_diff": 10, "cost_exp": 11, "cost_product": 12,
 }
 
 
@@ -67,6 +68,7 @@ def _lib():
     lib.orc_elems_brute.argtypes = [I, _u8p, _i32p, L, _i64p, _i32p, _u64p]
     lib.orc_reindex.argtypes = [L, _i64p, _i32p, _i64p, _i32p, _i32p]
     lib.orc_connected_patterns.argtypes = [I, _u8p, I]
+    lib.orc_clique_bitset_work.argtypes = [I, L, _i64p, _i32p, L, L, I, _u64p, _u64p]
     lib.orc_canonical_form.argtypes = [I, _u8p, _u8p]
     return lib
 
@@ -218,6 +220,19 @@ def reindex(g):
     _check(_lib().orc_reindex(g.n, rpp, colp, rp2.ctypes.data_as(_i64p),
                               col2.ctypes.data_as(_i32p), nid.ctypes.data_as(_i32p)), "reindex")
     return Csr(g.n, rp2, col2[:g.nnz], g.name + "_oriented"), nid[:g.n]
+
+
+def clique_bitset_work(k: int, g, root_lo: int = 0, root_hi: int | None = None,
+                       nthreads: int = 0):
+    """(count, words): the k-clique count found by the per-root bitset walk on the
+    reindexed graph g, and its 32-bit word operations (see gz_oracle.c). A work
+    measure for bitset kernels, not part of the method."""
+    rp, col, rpp, colp = _csr(g)
+    cnt, words = ctypes.c_uint64(), ctypes.c_uint64()
+    hi = g.n if root_hi is None else root_hi
+    _check(_lib().orc_clique_bitset_work(k, g.n, rpp, colp, root_lo, hi, nthreads, ctypes.byref(cnt),
+                                         ctypes.byref(words)), "clique_bitset_work")
+    return cnt.value, words.value
 
 
 def connected_patterns(k: int) -> list:

@@ -33,6 +33,11 @@
  *    orc_reindex: the orientation relabelling of Sec. 6 (higher degree gets a
  *      smaller id; ties by original id, ascending).
  *
+ *  Bitset work measure (for the roofline of bitset clique kernels)
+ *    orc_clique_bitset_work: the 32-bit word operations of the oriented
+ *      k-clique loops written over per-root bitsets (see its comment); also
+ *      returns the clique count the walk finds, as a check.
+ *
  *  Motifs (Sec. 7.1-7.2)
  *    orc_connected_patterns: every connected k-vertex graph up to isomorphism,
  *      by brute force over edge subsets and all k! relabellings.
@@ -75,7 +80,10 @@ enum {
     MUT_THM2_FIRST = 6,    /* Theorem 2 keeps the smallest z instead of the largest */
     MUT_AUT_NEXT_ONLY = 7, /* automorphism test only checks pairs (i, i+1) */
     MUT_REINDEX_ASC = 8,   /* orientation sorts degrees ascending */
-    MUT_E_FULL = 9         /* E counts whole lists, ignoring the bound */
+    MUT_E_FULL = 9,        /* E counts whole lists, ignoring the bound */
+    MUT_COST_NO_DIFF = 10, /* cost model drops the (1-p) factor of set differences */
+    MUT_COST_EXP = 11,     /* cost model raises p to #black + 1 */
+    MUT_COST_PRODUCT = 12  /* cost model multiplies the loops' costs instead of summing */
 };
 
 static int g_mut = 0;
@@ -318,10 +326,15 @@ double orc_cost(int k, const uint8_t* adj, const int32_t* order) {
             for (int j = 0; j < d; ++j) {
                 if (adj[order[d] * k + order[j]]) ++nb; else ++nr;
             }
+            if (g_mut == MUT_COST_NO_DIFF) nr = 0;
+            if (g_mut == MUT_COST_EXP) ++nb;
             iters = n * pow(p, (double)nb) * pow(1.0 - p, (double)nr);
         }
         prod *= iters;
-        cost += prod * orc_restriction_probability(k, bp, d);
+        if (g_mut == MUT_COST_PRODUCT)
+            cost = (d == 0 ? 1.0 : cost) * prod * orc_restriction_probability(k, bp, d);
+        else
+            cost += prod * orc_restriction_probability(k, bp, d);
     }
     return cost;
 }
@@ -693,6 +706,120 @@ int orc_reindex(int64_t n, const int64_t* rp, const int32_t* col, int64_t* rp_ou
 /* Edge test used by the tests' structural checks. */
 int orc_has_edge(const int64_t* rp, const int32_t* col, int32_t u, int32_t v) {
     return g_has_edge(rp, col, u, v);
+}
+
+/* -------------------------------------------------- bitset work measure */
+
+/*
+ * Work measure of the oriented k-clique count in bitset form. It is used to
+ * state a roofline for kernels that keep each root's candidate sets as
+ * bitsets; it is not part of the method, and no count the tests compare comes
+ * from it.
+ *
+ * On the degree-reindexed graph (Sec. 6) a k-clique's schedule bounds each
+ * loop by the one before it, so e_1, e_2, ... all lie in the root's out-list
+ * O = N(e_0) intersect [0, e_0), sorted. Relative to O, row(a) is the bitset
+ * {b < a : O[b] in N(O[a])}. Loop 2's candidate set for (e_1, e_2) = (O[a],
+ * O[b]) is row(a) AND row(b); each deeper loop ANDs the row of the index just
+ * chosen, and the last loop counts the set's bits. A set whose newest row is
+ * row(lim) holds bits below lim only, so it spans ceil(lim / 32) 32-bit words.
+ * One "word operation" produces one such word (the AND of the rows in it, then
+ * either a popcount or a walk over its bits). words_out sums, over every pair
+ * (a, b in row(a)) and every deeper partial clique, the words of the set it
+ * builds; building the rows and the loop over a are not included. count_out
+ * is the number of k-cliques the walk finds, which checks the walk against the
+ * plain count. Roots with |O| < k - 1 are skipped (they hold no k-clique).
+ * Graph: the reindexed CSR; roots in [root_lo, root_hi); 4 <= k <= 8.
+ */
+static void bits_level(const uint32_t* rows, int64_t W, const uint32_t* set, int32_t lim,
+                       int depth, uint32_t* scratch, uint64_t* words, uint64_t* cnt) {
+    const int64_t nw = ((int64_t)lim + 31) / 32;
+    *words += (uint64_t)nw;
+    if (depth == 1) {
+        for (int64_t w = 0; w < nw; ++w) *cnt += (uint64_t)__builtin_popcount(set[w]);
+        return;
+    }
+    uint32_t* next = scratch;
+    for (int64_t w = 0; w < nw; ++w) {
+        uint32_t bits = set[w];
+        while (bits) {
+            const int32_t c = (int32_t)(w * 32 + __builtin_ctz(bits));
+            bits &= bits - 1;
+            const uint32_t* rc = rows + (size_t)c * W;
+            const int64_t cw = ((int64_t)c + 31) / 32;
+            for (int64_t x = 0; x < cw; ++x) next[x] = set[x] & rc[x];
+            bits_level(rows, W, next, c, depth - 1, scratch + W, words, cnt);
+        }
+    }
+}
+
+int orc_clique_bitset_work(int k, int64_t n, const int64_t* rp, const int32_t* col,
+                           int64_t root_lo, int64_t root_hi, int threads, uint64_t* count_out,
+                           uint64_t* words_out) {
+    if (k < 4 || k > ORC_MAXK) return ORC_EINVAL;
+    if (root_lo < 0) root_lo = 0;
+    if (root_hi > n) root_hi = n;
+    int64_t maxout = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        int64_t d = 0;
+        for (int64_t i = rp[v]; i < rp[v + 1] && col[i] < v; ++i) ++d;
+        if (d > maxout) maxout = d;
+    }
+    const int64_t Wmax = (maxout + 31) / 32 + 1;
+    uint64_t cnt = 0, words = 0;
+    int err = 0;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#endif
+#pragma omp parallel reduction(+ : cnt, words)
+    {
+        uint32_t* rows = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(maxout + 1) * Wmax);
+        uint32_t* scratch = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(k + 1) * Wmax);
+        if (!rows || !scratch) {
+#pragma omp atomic write
+            err = 1;
+        } else {
+#pragma omp for schedule(dynamic, 64)
+            for (int64_t v = root_lo; v < root_hi; ++v) {
+                const int32_t* O = col + rp[v];
+                int64_t d = 0;
+                while (rp[v] + d < rp[v + 1] && O[d] < v) ++d;
+                if (d < k - 1) continue;
+                const int64_t W = (d + 31) / 32;
+                memset(rows, 0, sizeof(uint32_t) * (size_t)d * W);
+                /* row(a): merge O[0, a) with the out-list of O[a] (both sorted) */
+                for (int64_t a = 1; a < d; ++a) {
+                    const int32_t u = O[a];
+                    int64_t i = rp[u], b = 0;
+                    while (i < rp[u + 1] && col[i] < u && b < a) {
+                        if (col[i] < O[b]) ++i;
+                        else if (col[i] > O[b]) ++b;
+                        else { rows[a * W + b / 32] |= 1u << (b % 32); ++i; ++b; }
+                    }
+                }
+                uint32_t* set = scratch;
+                for (int64_t a = 1; a < d; ++a) {
+                    const uint32_t* ra = rows + a * W;
+                    for (int64_t wb = 0; wb < (a + 31) / 32; ++wb) {
+                        uint32_t bits = ra[wb];
+                        while (bits) {
+                            const int32_t b = (int32_t)(wb * 32 + __builtin_ctz(bits));
+                            bits &= bits - 1;
+                            const uint32_t* rb = rows + (size_t)b * W;
+                            for (int64_t x = 0; x < (b + 31) / 32; ++x) set[x] = ra[x] & rb[x];
+                            bits_level(rows, W, set, b, k - 3, scratch + Wmax, &words, &cnt);
+                        }
+                    }
+                }
+            }
+        }
+        free(rows);
+        free(scratch);
+    }
+    if (err) return ORC_ENOMEM;
+    *count_out = cnt;
+    *words_out = words;
+    return 0;
 }
 
 /* -------------------------------------------------------------- motifs */

@@ -29,6 +29,7 @@ EXPORTS = [
     "gz_plan_schedules", "gz_plan_describe", "gz_plan_destroy", "gz_count", "gz_count_ex", "gz_scratch_bytes",
     "gz_count_batch", "gz_count_noalloc", "gz_autotune", "gz_server_create", "gz_server_submit", "gz_server_wait",
     "gz_server_replay", "gz_server_destroy", "gz_last_error", "gz_version", "gz_kernel_launches",
+    "gz_allocations",
     "gz_motif_patterns", "gz_count_motifs", "gz_plan_create_measured", "gz_schedule_times",
 ]
 
@@ -77,6 +78,8 @@ def lib() -> ctypes.CDLL:
     L.gz_version.restype = ctypes.c_char_p
     L.gz_kernel_launches.restype = ctypes.c_uint64
     L.gz_kernel_launches.argtypes = []
+    L.gz_allocations.restype = ctypes.c_uint64
+    L.gz_allocations.argtypes = []
     sig = {
         "gz_load_csr": [_P, _P, I64, I64, I, ctypes.c_uint32, _P, ctypes.POINTER(_P)],
         "gz_orient": [_P, _P],
@@ -141,6 +144,11 @@ def _stream(stream) -> int | None:
 
 def version() -> str:
     return lib().gz_version().decode()
+
+
+def allocations() -> int:
+    """Memory allocation calls libgz has made in this process (gz_allocations)."""
+    return int(lib().gz_allocations())
 
 
 def kernel_launches() -> int:

@@ -21,6 +21,7 @@ thread_local char g_err[512] = "";
 }
 
 std::atomic<unsigned long long> g_launches{0};
+std::atomic<unsigned long long> g_allocs{0};
 
 void set_error(const char* fmt, ...) {
     va_list ap;
@@ -66,7 +67,7 @@ gz_status arena_reserve(Arena& a, uint64_t bytes) {
         a.bytes = 0;
     }
     uint64_t want = bytes < (64ull << 20) ? (64ull << 20) : bytes;
-    cudaError_t e = cudaMalloc(&a.ptr, want);
+    cudaError_t e = gz_malloc(&a.ptr, want);
     if (e != cudaSuccess) {
         a.ptr = nullptr;
         return cuda_fail(e, "scratch cudaMalloc");
@@ -200,15 +201,35 @@ LaunchCfg default_cfg() {
     return c;
 }
 
-uint64_t mixed_scratch_bytes(const Query* qs, int nq, const LaunchCfg& cfg) {
-    uint64_t words = 0;
+// Splits queries into those of the general kernel (with out_slot = their index;
+// cliques with out-lists past kCliqueLongOut keep their long roots there) and
+// the indices of those the clique kernels take.
+void split_kinds(const Query* qs, int nq, std::vector<Query>& gen, std::vector<int>* cliq) {
     for (int i = 0; i < nq; ++i) {
-        const Query& q = qs[i];
-        if (q.plan && clique_eligible(*q.prog, *q.plan, *q.view) && q.view->max_out <= kCliqueLongOut)
-            continue;
-        words = std::max(words, scratch_words_per_warp(*q.prog, *q.g, *q.view));
+        Query q = qs[i];
+        q.out_slot = i;
+        if (q.unit_hi <= q.unit_lo) continue;
+        if (q.plan && clique_eligible(*q.prog, *q.plan, *q.view)) {
+            if (cliq) cliq->push_back(i);
+            if (q.view->max_out <= kCliqueLongOut) continue;
+            q.min_root_out = kCliqueLongOut + 1;  // roots the bitset kernels leave out
+        }
+        gen.push_back(q);
     }
+}
+
+uint64_t mixed_scratch_bytes(const Query* qs, int nq, const LaunchCfg& cfg) {
+    std::vector<Query> gen;
+    split_kinds(qs, nq, gen, nullptr);
+    uint64_t words = 0;
+    for (const Query& q : gen) words = std::max(words, scratch_words_per_warp(*q.prog, *q.g, *q.view));
     return (uint64_t)resident_warps(cfg) * words * sizeof(int32_t);
+}
+
+uint64_t mixed_meta_bytes(const Query* qs, int nq) {
+    std::vector<Query> gen;
+    split_kinds(qs, nq, gen, nullptr);
+    return launch_meta_bytes(gen.data(), (int)gen.size());
 }
 
 // A small pool of streams per device on which one batch's queries overlap.
@@ -236,21 +257,14 @@ gz_status stream_pool(cudaStream_t** out) {
 
 gz_status launch_mixed(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream_t s,
                        unsigned long long* d_counts, int* d_status, unsigned long long* d_work,
-                       void* scratch, uint64_t scratch_bytes, bool overlap) {
+                       void* scratch, uint64_t scratch_bytes, void* meta, uint64_t meta_bytes,
+                       bool overlap) {
     std::vector<Query> gen;
     std::vector<int> cliq;
-    for (int i = 0; i < nq; ++i) {
-        Query q = qs[i];
-        q.out_slot = i;
-        if (q.unit_hi <= q.unit_lo) continue;
-        if (q.plan && clique_eligible(*q.prog, *q.plan, *q.view)) {
-            gz_status st = clique_prepare(*q.view, q.g->n, s);
-            if (st != GZ_OK) return st;
-            cliq.push_back(i);
-            if (q.view->max_out <= kCliqueLongOut) continue;
-            q.min_root_out = kCliqueLongOut + 1;  // roots the bitset kernels leave out
-        }
-        gen.push_back(q);
+    split_kinds(qs, nq, gen, &cliq);
+    for (int i : cliq) {
+        gz_status st = clique_prepare(*qs[i].view, qs[i].g->n, s);
+        if (st != GZ_OK) return st;
     }
     // one query (or one kind) runs on s; a mix of several forks onto the pool so
     // the general kernel and the clique launches overlap on the device
@@ -273,7 +287,8 @@ gz_status launch_mixed(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream
     if (!gen.empty()) {
         cudaStream_t t = fork(0);
         used.push_back(t);
-        st = count_launch(gen.data(), (int)gen.size(), cfg, t, d_counts, scratch, scratch_bytes, d_status);
+        st = count_launch(gen.data(), (int)gen.size(), cfg, t, d_counts, scratch, scratch_bytes, d_status,
+                          meta, meta_bytes);
     }
     for (size_t c = 0; c < cliq.size() && st == GZ_OK; ++c) {
         const Query& q = qs[cliq[c]];
@@ -297,33 +312,43 @@ gz_status launch_mixed(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream
     return st;
 }
 
-// Runs nq queries (one launch_mixed) and copies their counts to the host.
+// Runs nq queries and copies their counts to the host. All device state comes
+// from the library's scratch arena (grown when needed, then reused): a single
+// general-kernel query runs through count_one_in_region (descriptor as a kernel
+// parameter: one memset, the launches, one 16-byte read-back); anything else
+// through launch_mixed with the counts, descriptors and scratch in the arena.
 gz_status run_queries(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream_t s,
                       uint64_t* out_counts) {
-    const uint64_t need = mixed_scratch_bytes(qs, nq, cfg);
     Arena& a = arena();
     std::lock_guard<std::mutex> lk(a.mu);
+    if (nq == 1 && !(qs[0].plan && clique_eligible(*qs[0].prog, *qs[0].plan, *qs[0].view))) {
+        const Query& q = qs[0];
+        const uint64_t meta = one_meta_bytes(q, true);
+        const uint64_t scr = (uint64_t)resident_warps(cfg) * scratch_words_per_warp(*q.prog, *q.g, *q.view) * 4;
+        gz_status st = arena_reserve(a, meta + scr);
+        if (st != GZ_OK) return st;
+        return count_one_in_region(q, cfg, s, a.ptr, a.bytes - meta, true, out_counts);
+    }
+    // arena: counts [nq], status, clique work counters [3 nq] | launch metadata | scratch
+    const uint64_t head = ((sizeof(unsigned long long) * (4 * (uint64_t)nq + 1)) + 255) & ~255ull;
+    const uint64_t meta = (mixed_meta_bytes(qs, nq) + 255) & ~255ull;
+    const uint64_t need = head + meta + mixed_scratch_bytes(qs, nq, cfg);
     gz_status st = arena_reserve(a, need);
     if (st != GZ_OK) return st;
-    // counts [nq], status, clique work counters [3 nq]
-    const size_t words = (size_t)nq + 1 + 3 * (size_t)nq;
-    unsigned long long* d = nullptr;
-    cudaError_t e = cudaMallocAsync(&d, sizeof(unsigned long long) * words, s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync counts");
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(a.ptr);
+    char* mp = reinterpret_cast<char*>(a.ptr) + head;
     int* d_status = reinterpret_cast<int*>(d + nq);
-    e = cudaMemsetAsync(d, 0, sizeof(unsigned long long) * words, s);
-    if (e != cudaSuccess) {
-        cudaFreeAsync(d, s);
-        return cuda_fail(e, "memset counts");
-    }
-    st = launch_mixed(qs, nq, cfg, s, d, d_status, d + nq + 1, a.ptr, a.bytes, true);
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned long long) * (4 * (size_t)nq + 1), s);
+    if (e != cudaSuccess) return cuda_fail(e, "memset counts");
+    st = launch_mixed(qs, nq, cfg, s, d, d_status, d + nq + 1, mp + meta, a.bytes - head - meta, mp, meta, true);
     std::vector<unsigned long long> h(nq + 1);
     if (st == GZ_OK) {
         e = cudaMemcpyAsync(h.data(), d, sizeof(unsigned long long) * (nq + 1), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = cuda_fail(e, "count");
+    } else {
+        cudaStreamSynchronize(s);  // launches already queued must finish before the arena is reused
     }
-    cudaFreeAsync(d, s);
     if (st != GZ_OK) return st;
     if (*reinterpret_cast<int*>(&h[nq]) != 0) {
         set_error("count: a scratch buffer overflowed (planner capacity bug)");
@@ -352,6 +377,8 @@ const char* gz_version(void) { return "gz-gb300 0.1 (sm_103a)"; }
 
 uint64_t gz_kernel_launches(void) { return g_launches.load(); }
 
+uint64_t gz_allocations(void) { return g_allocs.load(); }
+
 gz_status gz_load_csr(const int64_t* row_ptr, const int32_t* col_idx, int64_t n, int64_t nnz,
                       int device_ptrs, uint32_t flags, void* stream, gz_graph** out) {
     GZ_RANGE("gz_load_csr");
@@ -378,8 +405,8 @@ gz_status gz_load_csr(const int64_t* row_ptr, const int32_t* col_idx, int64_t n,
         g->orig.col = const_cast<int32_t*>(col_idx);
         g->orig.owned_csr = false;
     } else {
-        e = cudaMalloc(&g->orig.rp, sizeof(int64_t) * (n + 1));
-        if (e == cudaSuccess) e = cudaMalloc(&g->orig.col, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+        e = gz_malloc(&g->orig.rp, sizeof(int64_t) * (n + 1));
+        if (e == cudaSuccess) e = gz_malloc(&g->orig.col, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
         if (e == cudaSuccess) e = cudaMemcpyAsync(g->orig.rp, row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess && nnz > 0)
             e = cudaMemcpyAsync(g->orig.col, col_idx, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, s);

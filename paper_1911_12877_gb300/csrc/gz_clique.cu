@@ -530,7 +530,7 @@ gz_status gather_heavy(GzView& v, int64_t n, cudaStream_t s) {
         return GZ_OK;
     }
     unsigned long long* cnt = nullptr;
-    cudaError_t e = cudaMallocAsync(&cnt, sizeof(unsigned long long), s);
+    cudaError_t e = gz_malloc_async(&cnt, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "clique: heavy roots");
     int64_t gb = (n + 255) / 256;
     const int grid = (int)std::min<int64_t>(gb, 152 * 16);
@@ -545,7 +545,7 @@ gz_status gather_heavy(GzView& v, int64_t n, cudaStream_t s) {
     int2* d_out = nullptr;
     std::vector<int2> tmp(h);
     if (e == cudaSuccess && h > 0) {
-        e = cudaMallocAsync(&d_out, sizeof(int2) * h, s);
+        e = gz_malloc_async(&d_out, sizeof(int2) * h, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s);
         if (e == cudaSuccess) {
             k_collect_heavy<<<grid, 256, 0, s>>>(v.dag_rp, n, kHeavyD, d_out, cnt, (int64_t)h);
@@ -602,10 +602,10 @@ gz_status build_heavy_rows(GzView& v, int mo, int sms, cudaStream_t s) {
         cudaFree(v.heavy_rows);
         v.heavy_rows = nullptr;
         v.heavy_rows_cap = 0;
-        e = cudaMalloc(&v.heavy_rows, sizeof(uint32_t) * words);
+        e = gz_malloc(&v.heavy_rows, sizeof(uint32_t) * words);
         if (e == cudaSuccess) v.heavy_rows_cap = words;
     }
-    if (e == cudaSuccess) e = cudaMallocAsync(&d_list, sizeof(int4) * list.size(), s);
+    if (e == cudaSuccess) e = gz_malloc_async(&d_list, sizeof(int4) * list.size(), s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_list, list.data(), sizeof(int4) * list.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
@@ -669,8 +669,8 @@ gz_status launch_long(GzView& v, int64_t lo, int64_t hi, cudaStream_t s,
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int4* d_l = nullptr;
     uint32_t* grows = nullptr;
-    cudaError_t e = cudaMallocAsync(&d_l, sizeof(int4) * (build.size() + ent.size()), s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&grows, sizeof(uint32_t) * words, s);
+    cudaError_t e = gz_malloc_async(&d_l, sizeof(int4) * (build.size() + ent.size()), s);
+    if (e == cudaSuccess) e = gz_malloc_async(&grows, sizeof(uint32_t) * words, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(grows, 0, sizeof(uint32_t) * words, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_l, build.data(), sizeof(int4) * build.size(), cudaMemcpyHostToDevice, s);
@@ -740,7 +740,7 @@ gz_status launch_k(const GzView& v, int64_t n, int64_t lo, int64_t hi, cudaStrea
     int4* d_ent = nullptr;
     cudaError_t e = cudaSuccess;
     if (!ent.empty()) {
-        e = cudaMallocAsync(&d_ent, sizeof(int4) * ent.size(), s);
+        e = gz_malloc_async(&d_ent, sizeof(int4) * ent.size(), s);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(d_ent, ent.data(), sizeof(int4) * ent.size(), cudaMemcpyHostToDevice, s);
     }

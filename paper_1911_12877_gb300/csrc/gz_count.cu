@@ -24,6 +24,8 @@
 #include <climits>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "gz_internal.h"
@@ -92,14 +94,11 @@ uint64_t scratch_layout(const GzProg& p, const gz_graph& g, const GzView& v, KQ*
 }
 
 // Splitting of heavy units. A unit whose loop-2 candidate list holds at least
-// kSplitMin vertices is not run by the warp that popped it: the first pass
-// records it (launch-space unit index and candidate count), a one-CTA scan
-// turns the records into chunks of kSplitChunk candidates, and a second pass
-// hands the chunks to warps, each recomputing loop 1 and walking its chunk of
-// loop 2. A hub edge then spreads over many warps instead of holding one.
-constexpr int64_t kSplitMin = 512;
-constexpr int64_t kSplitChunk = 256;
-
+// LaunchCfg::split_min vertices is not run by the warp that popped it: the first
+// pass records it (launch-space unit index and candidate count), a one-CTA scan
+// turns the records into chunks of LaunchCfg::split_chunk candidates, and a
+// second pass hands the chunks to warps, each recomputing loop 1 and walking its
+// chunk of loop 2. A hub edge then spreads over many warps instead of holding one.
 struct Deferred {
     int64_t unit;  // launch-space unit index
     int64_t n2;    // loop-2 candidates
@@ -109,6 +108,7 @@ struct DeferCtl {
     Deferred* list;              // NULL: no deferral
     unsigned long long* count;   // records written (may exceed cap)
     int64_t cap;
+    int64_t min_n2;              // loop-2 candidates from which a unit is deferred
 };
 
 // Number of elements of sorted L[0, n) that are < beta (warp-cooperative
@@ -576,7 +576,7 @@ __device__ void last_level_flat(const KQ& q, const GzOp& op, WarpState& ws, List
 }
 
 // Runs one unit (e0, e1), loop 2 restricted to candidates [lo2, hi2) (hi2 < 0:
-// all). With df.list set, a unit with at least kSplitMin loop-2 candidates is
+// all). With df.list set, a unit with at least df.min_n2 loop-2 candidates is
 // recorded for the split pass instead (u = its launch-space index).
 __device__ void process_unit(const KQ& q, int64_t unit, WarpState& ws, int32_t* scratch,
                              int32_t* sm, int lane, unsigned long long& acc, int* status,
@@ -597,7 +597,7 @@ __device__ void process_unit(const KQ& q, int64_t unit, WarpState& ws, int32_t* 
     run_level(q, 1, ws, scratch, lane, acc, status);
     if (k == 3) return;
     const ListRef c2 = cand_list(q, 2, ws, scratch, lane);
-    if (df && df->list && c2.n >= kSplitMin) {
+    if (df && df->list && c2.n >= df->min_n2) {
         unsigned long long slot = 0;
         if (lane == 0) slot = atomicAdd(df->count, 1ull);
         slot = __shfl_sync(kFull, slot, 0);
@@ -702,13 +702,14 @@ __global__ void __launch_bounds__(256, 2) k_enumerate(const KQ* __restrict__ qs,
 // the min(count, cap) records of the first pass; prefix[n] = all chunks. One CTA.
 __global__ void __launch_bounds__(1024) k_split_scan(const Deferred* __restrict__ dl,
                                                      const unsigned long long* __restrict__ dcount,
-                                                     int64_t cap, int64_t* __restrict__ prefix) {
+                                                     int64_t cap, int64_t chunk,
+                                                     int64_t* __restrict__ prefix) {
     __shared__ int64_t part[1024];
     const int64_t n = (int64_t)*dcount < cap ? (int64_t)*dcount : cap;
     const int64_t per = (n + 1023) / 1024;
     const int64_t b = threadIdx.x * per, e = b + per < n ? b + per : n;
     int64_t sum = 0;
-    for (int64_t i = b; i < e; ++i) sum += (dl[i].n2 + kSplitChunk - 1) / kSplitChunk;
+    for (int64_t i = b; i < e; ++i) sum += (dl[i].n2 + chunk - 1) / chunk;
     part[threadIdx.x] = sum;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -724,7 +725,7 @@ __global__ void __launch_bounds__(1024) k_split_scan(const Deferred* __restrict_
     int64_t run = part[threadIdx.x];
     for (int64_t i = b; i < e; ++i) {
         prefix[i] = run;
-        run += (dl[i].n2 + kSplitChunk - 1) / kSplitChunk;
+        run += (dl[i].n2 + chunk - 1) / chunk;
     }
 }
 
@@ -734,6 +735,7 @@ __global__ void __launch_bounds__(256, 2) k_enumerate_split(const KQ* __restrict
                                                          const unsigned long long* __restrict__ dcount,
                                                          int64_t cap,
                                                          const int64_t* __restrict__ prefix,
+                                                         int64_t chunk,
                                                          unsigned long long* __restrict__ work,
                                                          unsigned long long* __restrict__ counts,
                                                          int* __restrict__ status,
@@ -760,7 +762,7 @@ __global__ void __launch_bounds__(256, 2) k_enumerate_split(const KQ* __restrict
             if (prefix[mid] <= (int64_t)t) lo = mid; else hi = mid - 1;
         }
         const Deferred rec = dl[lo];
-        const int64_t c0 = ((int64_t)t - prefix[lo]) * kSplitChunk;
+        const int64_t c0 = ((int64_t)t - prefix[lo]) * chunk;
         const int64_t u = rec.unit;
         if (cur < 0 || u < qs[cur].unit_begin || u >= qs[cur].unit_begin + qs[cur].unit_count) {
             if (cur >= 0) {
@@ -777,7 +779,7 @@ __global__ void __launch_bounds__(256, 2) k_enumerate_split(const KQ* __restrict
         }
         const KQ& q = qs[cur];
         process_unit(q, q.unit_lo + (u - q.unit_begin), ws, my, sm, lane, acc, status, c0,
-                     c0 + kSplitChunk);
+                     c0 + chunk);
     }
     if (cur >= 0) {
         unsigned long long s = warp_sum(acc);
@@ -786,16 +788,17 @@ __global__ void __launch_bounds__(256, 2) k_enumerate_split(const KQ* __restrict
 }
 
 // Single-query form of k_enumerate: the descriptor travels as a kernel
-// parameter and all device state (queue counter, count, status, per-warp
-// scratch) lives in one caller-provided region, so launching it needs no
-// device allocation.
+// parameter (no descriptor copy) and all device state (queue counters, count,
+// status, deferred records, per-warp scratch) lives in one region the caller
+// provides, so a count allocates nothing. With df.list set, heavy units are
+// recorded for k_enumerate_split_one as in k_enumerate.
 __global__ void __launch_bounds__(256, 2) k_enumerate_one(const __grid_constant__ KQ q,
                                                        int64_t total_units, int chunk,
                                                        unsigned long long* __restrict__ work,
                                                        unsigned long long* __restrict__ count,
                                                        int* __restrict__ status,
                                                        int32_t* __restrict__ scratch,
-                                                       int64_t words_per_warp) {
+                                                       int64_t words_per_warp, DeferCtl df) {
     extern __shared__ int32_t smem[];
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -810,7 +813,46 @@ __global__ void __launch_bounds__(256, 2) k_enumerate_one(const __grid_constant_
         if ((int64_t)start >= total_units) break;
         int64_t end = (int64_t)start + chunk;
         if (end > total_units) end = total_units;
-        for (int64_t u = (int64_t)start; u < end; ++u) process_unit(q, q.unit_lo + u, ws, my, sm, lane, acc, status);
+        for (int64_t u = (int64_t)start; u < end; ++u)
+            process_unit(q, q.unit_lo + u, ws, my, sm, lane, acc, status, 0, -1, &df, u);
+    }
+    unsigned long long s = warp_sum(acc);
+    if (lane == 0 && s) atomicAdd(count, s);
+}
+
+// Second pass of k_enumerate_one: chunk t of the deferred units, one per warp pop.
+__global__ void __launch_bounds__(256, 2) k_enumerate_split_one(const __grid_constant__ KQ q,
+                                                             const Deferred* __restrict__ dl,
+                                                             const unsigned long long* __restrict__ dcount,
+                                                             int64_t cap,
+                                                             const int64_t* __restrict__ prefix,
+                                                             int64_t chunk,
+                                                             unsigned long long* __restrict__ work,
+                                                             unsigned long long* __restrict__ count,
+                                                             int* __restrict__ status,
+                                                             int32_t* __restrict__ scratch,
+                                                             int64_t words_per_warp) {
+    extern __shared__ int32_t smem[];
+    const int lane = threadIdx.x & 31;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int32_t* my = scratch + gwarp * words_per_warp;
+    int32_t* sm = smem + (threadIdx.x >> 5) * kWarpSmemWords;
+    const int64_t n = (int64_t)*dcount < cap ? (int64_t)*dcount : cap;
+    const int64_t total = prefix[n];
+    WarpState ws;
+    unsigned long long acc = 0;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(work, 1ull);
+        t = __shfl_sync(kFull, t, 0);
+        if ((int64_t)t >= total) break;
+        int64_t lo = 0, hi = n - 1;  // last record with prefix <= t
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= (int64_t)t) lo = mid; else hi = mid - 1;
+        }
+        const int64_t c0 = ((int64_t)t - prefix[lo]) * chunk;
+        process_unit(q, q.unit_lo + dl[lo].unit, ws, my, sm, lane, acc, status, c0, c0 + chunk);
     }
     unsigned long long s = warp_sum(acc);
     if (lane == 0 && s) atomicAdd(count, s);
@@ -830,33 +872,92 @@ void fill_kq(const Query& Q, KQ& k, uint64_t* words_out) {
     *words_out = scratch_layout(*Q.prog, *Q.g, v, &k);
 }
 
+// Dynamic shared memory of a CTA of bw warps, and the limit raised once per
+// device for each enumeration kernel (8 warps, above the 48 KB default).
+inline size_t cta_smem(int bw) { return (size_t)bw * kWarpSmemWords * 4; }
+std::atomic<unsigned long long> g_attr_enum{0}, g_attr_split{0}, g_attr_one{0}, g_attr_split_one{0};
+
+cudaError_t enum_attrs() {
+    const int b = (int)cta_smem(8);
+    cudaError_t e = smem_attr_once(k_enumerate, b, g_attr_enum);
+    if (e == cudaSuccess) e = smem_attr_once(k_enumerate_split, b, g_attr_split);
+    if (e == cudaSuccess) e = smem_attr_once(k_enumerate_one, b, g_attr_one);
+    if (e == cudaSuccess) e = smem_attr_once(k_enumerate_split_one, b, g_attr_split_one);
+    return e;
+}
+
+// SM count and resident CTAs per SM of k_enumerate for each block size, per
+// device, looked up once (the occupancy query costs microseconds per call).
+struct OccKey {
+    int dev, bw;
+    bool operator<(const OccKey& o) const { return dev != o.dev ? dev < o.dev : bw < o.bw; }
+};
+std::mutex g_occ_mu;
+std::map<OccKey, std::pair<int, int>> g_occ;
+
+gz_status grid_shape(int bw, int* sms_out, int* per_sm_out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "count: cudaGetDevice");
+    {
+        std::lock_guard<std::mutex> lk(g_occ_mu);
+        auto it = g_occ.find(OccKey{dev, bw});
+        if (it != g_occ.end()) {
+            *sms_out = it->second.first;
+            *per_sm_out = it->second.second;
+            return GZ_OK;
+        }
+    }
+    e = enum_attrs();
+    if (e != cudaSuccess) return cuda_fail(e, "count: kernel shared-memory attribute");
+    int sms = 0, per_sm = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate, bw * 32, cta_smem(bw));
+    if (e != cudaSuccess) return cuda_fail(e, "count: occupancy");
+    if (per_sm < 1) per_sm = 1;
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    g_occ[OccKey{dev, bw}] = {sms, per_sm};
+    *sms_out = sms;
+    *per_sm_out = per_sm;
+    return GZ_OK;
+}
+
+inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+
+// Deferred-record capacity of a launch over `units` work units.
+inline int64_t defer_cap(int64_t units) { return std::min<int64_t>(units, (int64_t)1 << 20); }
+
 }  // namespace
 
-// Counts one query with every piece of device state inside `region`
-// (kRegionHeader bytes of counters, then scratch_bytes of per-warp scratch);
-// launches fewer warps when the scratch would not hold a full grid. Allocates
-// nothing. Synchronous: the count and status are read back into host locals.
+// Bytes of a single-query region before its scratch: the counters, then (with
+// splitting) the deferred records and the chunk prefix.
+uint64_t one_meta_bytes(const Query& Q, bool split) {
+    if (!split || Q.prog->k < 4) return kRegionHeader;
+    const int64_t cap = defer_cap(Q.unit_hi - Q.unit_lo);
+    return kRegionHeader + align256(sizeof(Deferred) * cap) + align256(sizeof(int64_t) * (cap + 1));
+}
+
+// Counts one query with every piece of device state inside `region`:
+// one_meta_bytes(Q, split) bytes of counters (pass-1 queue, count, status,
+// pass-2 queue, deferred-record count) and deferred records, then scratch_bytes
+// of per-warp scratch. Launches fewer warps when the scratch would not hold a
+// full grid. Allocates nothing. Synchronous: the count and status are read back
+// into host locals. split = false runs no second pass (every unit in the first).
 gz_status count_one_in_region(const Query& Q, const LaunchCfg& cfg, cudaStream_t s, void* region,
-                              uint64_t scratch_bytes, uint64_t* out_count) {
+                              uint64_t scratch_bytes, bool split, uint64_t* out_count) {
     KQ k;
     uint64_t words = 0;
     fill_kq(Q, k, &words);
     const int64_t total = Q.unit_hi - Q.unit_lo;
     *out_count = 0;
     if (total <= 0) return GZ_OK;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int bw = cfg.block_warps;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_enumerate_one, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             8 * kWarpSmemWords * 4);
-        attr = true;
-    }
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate_one, bw * 32, bw * kWarpSmemWords * 4);
-    if (per_sm < 1) per_sm = 1;
+    split = split && Q.prog->k >= 4;
+    int bw = cfg.block_warps, sms = 0, per_sm = 0;
+    gz_status st = grid_shape(bw, &sms, &per_sm);
+    if (st != GZ_OK) return st;
     int64_t warps = (int64_t)sms * per_sm * bw;
+    if (cfg.blocks > 0) warps = (int64_t)cfg.blocks * bw;
     if (words > 0) {
         const int64_t fit = (int64_t)(scratch_bytes / (words * sizeof(int32_t)));
         if (fit < 1) {
@@ -868,24 +969,41 @@ gz_status count_one_in_region(const Query& Q, const LaunchCfg& cfg, cudaStream_t
     }
     if (warps < bw) bw = (int)warps;
     const int blocks = (int)(warps / bw);
+    char* base = reinterpret_cast<char*>(region);
     unsigned long long* hdr = reinterpret_cast<unsigned long long*>(region);
+    int* status = reinterpret_cast<int*>(hdr + 2);
+    const uint64_t meta = one_meta_bytes(Q, split);
+    int32_t* scratch = reinterpret_cast<int32_t*>(base + meta);
+    const int64_t cap = split ? defer_cap(total) : 0;
+    Deferred* dl = split ? reinterpret_cast<Deferred*>(base + kRegionHeader) : nullptr;
+    int64_t* prefix = split ? reinterpret_cast<int64_t*>(base + kRegionHeader + align256(sizeof(Deferred) * cap))
+                            : nullptr;
+    const int chunk = cfg.chunk > 0 ? cfg.chunk : 1;
     cudaError_t e = cudaMemsetAsync(region, 0, kRegionHeader, s);
     if (e == cudaSuccess) {
-        k_enumerate_one<<<blocks, bw * 32, bw * kWarpSmemWords * 4, s>>>(
-            k, total, cfg.chunk > 0 ? cfg.chunk : 1, hdr, hdr + 1, reinterpret_cast<int*>(hdr + 2),
-            reinterpret_cast<int32_t*>(reinterpret_cast<char*>(region) + kRegionHeader), (int64_t)words);
+        DeferCtl df{dl, hdr + 4, cap, cfg.split_min};
+        k_enumerate_one<<<blocks, bw * 32, cta_smem(bw), s>>>(k, total, chunk, hdr, hdr + 1, status, scratch,
+                                                             (int64_t)words, df);
         GZ_COUNT_LAUNCH();
+        if (split) {
+            k_split_scan<<<1, 1024, 0, s>>>(dl, hdr + 4, cap, cfg.split_chunk, prefix);
+            GZ_COUNT_LAUNCH();
+            k_enumerate_split_one<<<blocks, bw * 32, cta_smem(bw), s>>>(k, dl, hdr + 4, cap, prefix,
+                                                                       cfg.split_chunk, hdr + 3, hdr + 1,
+                                                                       status, scratch, (int64_t)words);
+            GZ_COUNT_LAUNCH();
+        }
         e = cudaGetLastError();
     }
-    unsigned long long h[3] = {0, 0, 0};
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h, hdr, sizeof(h), cudaMemcpyDeviceToHost, s);
+    unsigned long long h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, hdr + 1, sizeof(h), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "count (region)");
-    if ((int)h[2] != 0) {
+    if ((int)h[1] != 0) {
         set_error("count: a scratch buffer overflowed (planner capacity bug)");
         return GZ_EOVERFLOW;
     }
-    *out_count = h[1];
+    *out_count = h[0];
     return GZ_OK;
 }
 
@@ -894,28 +1012,38 @@ uint64_t scratch_words_per_warp(const GzProg& p, const gz_graph& g, const GzView
 }
 
 int resident_warps(const LaunchCfg& cfg) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_enumerate, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             8 * kWarpSmemWords * 4);
-        attr = true;
+    int sms = 0, per_sm = 0;
+    if (grid_shape(cfg.block_warps, &sms, &per_sm) != GZ_OK) {
+        sms = 1;
+        per_sm = 1;
     }
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate, cfg.block_warps * 32,
-                                                  cfg.block_warps * kWarpSmemWords * 4);
-    if (per_sm < 1) per_sm = 1;
-    int blocks = cfg.blocks > 0 ? cfg.blocks : sms * per_sm;
+    const int blocks = cfg.blocks > 0 ? cfg.blocks : sms * per_sm;
     return blocks * cfg.block_warps;
+}
+
+// Device bytes count_launch needs beside the scratch: the query descriptors,
+// four counters, and (when some query has k >= 4) the deferred records and
+// their chunk prefix.
+uint64_t launch_meta_bytes(const Query* qs, int nq) {
+    if (nq <= 0) return 0;
+    int64_t total = 0;
+    bool split = false;
+    for (int i = 0; i < nq; ++i) {
+        total += qs[i].unit_hi - qs[i].unit_lo;
+        split = split || qs[i].prog->k >= 4;
+    }
+    const int64_t cap = split ? defer_cap(total) : 0;
+    return align256(sizeof(KQ) * nq) + 256 + align256(sizeof(Deferred) * cap) +
+           align256(sizeof(int64_t) * (cap + 1));
 }
 
 // Builds the per-query descriptors, then one persistent launch. d_counts[nq] must
 // be zeroed by the caller (on stream s); scratch must hold resident_warps(cfg) *
-// max words per warp int32 words.
+// max words per warp int32 words; meta must hold launch_meta_bytes(qs, nq) bytes
+// (256-byte aligned). Allocates nothing.
 gz_status count_launch(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream_t s,
                        unsigned long long* d_counts, void* scratch, uint64_t scratch_bytes,
-                       int* d_status) {
+                       int* d_status, void* meta, uint64_t meta_bytes) {
     if (nq <= 0) return GZ_OK;
     std::vector<KQ> h(nq);
     int64_t total = 0;
@@ -923,20 +1051,12 @@ gz_status count_launch(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream
     for (int i = 0; i < nq; ++i) {
         const Query& Q = qs[i];
         KQ& k = h[i];
-        memset(&k, 0, sizeof(KQ));
-        k.prog = *Q.prog;
-        const GzView& v = *Q.view;
-        k.rp = v.rp; k.col = v.col; k.drp = v.dag_rp; k.dcol = v.dag_col;
-        if (Q.prog->unit_dag) { k.usrc = v.dag_src; k.ucol = v.dag_col; k.urp = v.dag_rp; }
-        else { k.usrc = v.src; k.ucol = v.col; k.urp = v.rp; }
-        k.unit_lo = Q.unit_lo;
-        k.unit_count = Q.unit_hi - Q.unit_lo;
+        uint64_t w = 0;
+        fill_kq(Q, k, &w);
         k.unit_begin = total;
-        k.min_root_out = Q.min_root_out;
         k.out_slot = Q.out_slot >= 0 ? Q.out_slot : i;
         total += k.unit_count;
-        const uint64_t off = scratch_layout(*Q.prog, *Q.g, v, &k);
-        if (off > words) words = off;
+        if (w > words) words = w;
     }
     if (total == 0) return GZ_OK;
     const int warps = resident_warps(cfg);
@@ -945,46 +1065,40 @@ gz_status count_launch(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream
                   (unsigned long long)((uint64_t)warps * words * 4));
         return GZ_ENOMEM;
     }
-    // one allocation: queries | 4 counters (pass-1 queue, pass-2 queue, records) |
+    if (meta_bytes < launch_meta_bytes(qs, nq)) {
+        set_error("count: launch metadata region too small");
+        return GZ_ENOMEM;
+    }
+    // meta: queries | 4 counters (pass-1 queue, pass-2 queue, records) |
     // deferred records [cap] | chunk prefix [cap + 1]
     bool split = false;
     for (int i = 0; i < nq; ++i) split = split || qs[i].prog->k >= 4;
-    const int64_t cap = split ? std::min<int64_t>(total, (int64_t)1 << 20) : 0;
-    const size_t qbytes = (sizeof(KQ) * nq + 255) & ~(size_t)255;
-    const size_t bytes = qbytes + 32 + sizeof(Deferred) * cap + sizeof(int64_t) * (cap + 1);
-    char* base = nullptr;
-    cudaError_t e = cudaMallocAsync(&base, bytes, s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync queries");
+    const int64_t cap = split ? defer_cap(total) : 0;
+    char* base = reinterpret_cast<char*>(meta);
+    const uint64_t qbytes = align256(sizeof(KQ) * nq);
     KQ* d = reinterpret_cast<KQ*>(base);
     unsigned long long* work = reinterpret_cast<unsigned long long*>(base + qbytes);
-    Deferred* dl = reinterpret_cast<Deferred*>(base + qbytes + 32);
-    int64_t* prefix = reinterpret_cast<int64_t*>(dl + cap);
-    e = cudaMemcpyAsync(d, h.data(), sizeof(KQ) * nq, cudaMemcpyHostToDevice, s);
+    Deferred* dl = reinterpret_cast<Deferred*>(base + qbytes + 256);
+    int64_t* prefix = reinterpret_cast<int64_t*>(base + qbytes + 256 + align256(sizeof(Deferred) * cap));
+    cudaError_t e = cudaMemcpyAsync(d, h.data(), sizeof(KQ) * nq, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(work, 0, 32, s);
     if (e == cudaSuccess) {
         const int blocks = warps / cfg.block_warps;
-        DeferCtl df{split ? dl : nullptr, work + 2, cap};
-        k_enumerate<<<blocks, cfg.block_warps * 32, cfg.block_warps * kWarpSmemWords * 4, s>>>(
+        DeferCtl df{split ? dl : nullptr, work + 2, cap, cfg.split_min};
+        k_enumerate<<<blocks, cfg.block_warps * 32, cta_smem(cfg.block_warps), s>>>(
             d, nq, total, cfg.chunk > 0 ? cfg.chunk : 1, work, d_counts, d_status,
             reinterpret_cast<int32_t*>(scratch), (int64_t)words, df);
         GZ_COUNT_LAUNCH();
         if (split) {
-            k_split_scan<<<1, 1024, 0, s>>>(dl, work + 2, cap, prefix);
+            k_split_scan<<<1, 1024, 0, s>>>(dl, work + 2, cap, cfg.split_chunk, prefix);
             GZ_COUNT_LAUNCH();
-            static bool attr = false;
-            if (!attr) {
-                cudaFuncSetAttribute(k_enumerate_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     8 * kWarpSmemWords * 4);
-                attr = true;
-            }
-            k_enumerate_split<<<blocks, cfg.block_warps * 32, cfg.block_warps * kWarpSmemWords * 4, s>>>(
-                d, nq, dl, work + 2, cap, prefix, work + 1, d_counts, d_status,
+            k_enumerate_split<<<blocks, cfg.block_warps * 32, cta_smem(cfg.block_warps), s>>>(
+                d, nq, dl, work + 2, cap, prefix, cfg.split_chunk, work + 1, d_counts, d_status,
                 reinterpret_cast<int32_t*>(scratch), (int64_t)words);
             GZ_COUNT_LAUNCH();
         }
         e = cudaGetLastError();
     }
-    cudaFreeAsync(base, s);
     if (e != cudaSuccess) return cuda_fail(e, "enumerate launch");
     return GZ_OK;
 }

@@ -95,7 +95,7 @@ cudaError_t exclusive_scan(const int64_t* in, int64_t* out, int64_t n, cudaStrea
         return cudaGetLastError();
     }
     int64_t* sums = nullptr;
-    cudaError_t e = cudaMallocAsync(&sums, sizeof(int64_t) * tiles, s);
+    cudaError_t e = gz_malloc_async(&sums, sizeof(int64_t) * tiles, s);
     if (e != cudaSuccess) return e;
     scan_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, sums);
     GZ_COUNT_LAUNCH();
@@ -190,7 +190,7 @@ cudaError_t radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t*
     if (n <= 1 || bits <= 0) return cudaSuccess;
     int64_t ntiles = (n + kTile - 1) / kTile;
     int64_t* hist = nullptr;
-    cudaError_t e = cudaMallocAsync(&hist, sizeof(int64_t) * 256 * ntiles, s);
+    cudaError_t e = gz_malloc_async(&hist, sizeof(int64_t) * 256 * ntiles, s);
     if (e != cudaSuccess) return e;
     int passes = (bits + 7) / 8;
     for (int p = 0; p < passes && e == cudaSuccess; ++p) {
@@ -380,7 +380,7 @@ int bits_for(uint64_t x) {
 // Device-wide helpers used by the API layer.
 gz_status max_degree(const int64_t* rp, int64_t n, int64_t* out, cudaStream_t s) {
     unsigned long long* d = nullptr;
-    cudaError_t e = cudaMallocAsync(&d, sizeof(unsigned long long), s);
+    cudaError_t e = gz_malloc_async(&d, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
     cudaMemsetAsync(d, 0, sizeof(unsigned long long), s);
     if (n > 0) {
@@ -412,7 +412,7 @@ gz_status validate_csr(const int64_t* rp, const int32_t* col, int64_t n, int64_t
     }
     if (n == 0) return GZ_OK;
     unsigned long long* err = nullptr;
-    e = cudaMallocAsync(&err, sizeof(unsigned long long) * 5, s);
+    e = gz_malloc_async(&err, sizeof(unsigned long long) * 5, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
     cudaMemsetAsync(err, 0, sizeof(unsigned long long) * 5, s);
     k_validate<<<warp_grid(n), kThreads, 0, s>>>(rp, col, n, nnz, symmetric ? 1 : 0, err);
@@ -438,11 +438,11 @@ gz_status build_dag(gz_graph* g, GzView* v, cudaStream_t s) {
     const int64_t n = g->n;
     cudaError_t e;
     if (!v->dag_rp) {  // kept across rebuilds of the view (same n)
-        e = cudaMalloc(&v->dag_rp, sizeof(int64_t) * (n + 1));
+        e = gz_malloc(&v->dag_rp, sizeof(int64_t) * (n + 1));
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc dag_rp");
     }
     unsigned long long* mx = nullptr;
-    e = cudaMallocAsync(&mx, sizeof(unsigned long long), s);
+    e = gz_malloc_async(&mx, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
     cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s);
     cudaMemsetAsync(v->dag_rp + n, 0, sizeof(int64_t), s);
@@ -467,8 +467,8 @@ gz_status build_dag(gz_graph* g, GzView* v, cudaStream_t s) {
         v->dag_src = nullptr;
         v->dag_cap = 0;
         const size_t bytes = sizeof(int32_t) * (size_t)need;
-        e = cudaMalloc(&v->dag_col, bytes);
-        if (e == cudaSuccess) e = cudaMalloc(&v->dag_src, bytes);
+        e = gz_malloc(&v->dag_col, bytes);
+        if (e == cudaSuccess) e = gz_malloc(&v->dag_src, bytes);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc dag");
         v->dag_cap = need;
     }
@@ -486,7 +486,7 @@ gz_status build_dag(gz_graph* g, GzView* v, cudaStream_t s) {
 
 gz_status build_src(gz_graph* g, GzView* v, cudaStream_t s) {
     if (v->src) return GZ_OK;
-    cudaError_t e = cudaMalloc(&v->src, sizeof(int32_t) * (size_t)(g->nnz > 0 ? g->nnz : 1));
+    cudaError_t e = gz_malloc(&v->src, sizeof(int32_t) * (size_t)(g->nnz > 0 ? g->nnz : 1));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc src");
     if (g->n > 0) {
         k_src<<<warp_grid(g->n), kThreads, 0, s>>>(v->rp, g->n, v->src);
@@ -513,9 +513,9 @@ gz_status orient(gz_graph* g, cudaStream_t s) {
         if (e != cudaSuccess) return cuda_fail(e, "gz_orient: wait for running counts");
     }
     if (!o.rp) {
-        e = cudaMalloc(&o.rp, sizeof(int64_t) * (n + 1));
-        if (e == cudaSuccess) e = cudaMalloc(&o.col, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
-        if (e == cudaSuccess) e = cudaMalloc(&g->new_id, sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+        e = gz_malloc(&o.rp, sizeof(int64_t) * (n + 1));
+        if (e == cudaSuccess) e = gz_malloc(&o.col, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+        if (e == cudaSuccess) e = gz_malloc(&g->new_id, sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc oriented CSR");
     }
     if (n == 0) {
@@ -526,15 +526,15 @@ gz_status orient(gz_graph* g, cudaStream_t s) {
     const int64_t m2 = nnz > n ? nnz : n;
     uint32_t *k0 = nullptr, *v0 = nullptr, *k1 = nullptr, *v1 = nullptr;
     int64_t *deg = nullptr, *ndeg = nullptr;
-    e = cudaMallocAsync(&k0, sizeof(uint32_t) * m2, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&v0, sizeof(uint32_t) * m2, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&k1, sizeof(uint32_t) * m2, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&v1, sizeof(uint32_t) * m2, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&deg, sizeof(int64_t) * (n + 1), s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&ndeg, sizeof(int64_t) * (n + 1), s);
+    e = gz_malloc_async(&k0, sizeof(uint32_t) * m2, s);
+    if (e == cudaSuccess) e = gz_malloc_async(&v0, sizeof(uint32_t) * m2, s);
+    if (e == cudaSuccess) e = gz_malloc_async(&k1, sizeof(uint32_t) * m2, s);
+    if (e == cudaSuccess) e = gz_malloc_async(&v1, sizeof(uint32_t) * m2, s);
+    if (e == cudaSuccess) e = gz_malloc_async(&deg, sizeof(int64_t) * (n + 1), s);
+    if (e == cudaSuccess) e = gz_malloc_async(&ndeg, sizeof(int64_t) * (n + 1), s);
     gz_status st = GZ_OK;
     unsigned long long* bad = nullptr;
-    if (e == cudaSuccess) e = cudaMallocAsync(&bad, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = gz_malloc_async(&bad, sizeof(unsigned long long), s);
     if (e != cudaSuccess) { st = cuda_fail(e, "gz_orient: temporaries"); goto done; }
     {
         cudaMemsetAsync(bad, 0, sizeof(unsigned long long), s);
@@ -558,7 +558,7 @@ gz_status orient(gz_graph* g, cudaStream_t s) {
         // keys/vals for the edge sort reuse k1/v1 and a second pair from k0 after
         // copying the order out of v0
         uint32_t* order_copy = nullptr;
-        e = cudaMallocAsync(&order_copy, sizeof(uint32_t) * n, s);
+        e = gz_malloc_async(&order_copy, sizeof(uint32_t) * n, s);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(order_copy, order, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) { st = cuda_fail(e, "gz_orient: order copy"); goto done; }

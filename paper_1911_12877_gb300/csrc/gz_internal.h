@@ -124,6 +124,41 @@ struct NvtxRange {
 extern std::atomic<unsigned long long> g_launches;
 #define GZ_COUNT_LAUNCH() (::gz::g_launches.fetch_add(1, std::memory_order_relaxed))
 
+// Memory allocation calls (device, stream-ordered and pinned host) this library
+// has made in this process. Every allocation of the library goes through these
+// wrappers, so a caller can check that a path allocated nothing.
+extern std::atomic<unsigned long long> g_allocs;
+template <typename T>
+inline cudaError_t gz_malloc(T** p, size_t bytes) {
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
+    return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+template <typename T>
+inline cudaError_t gz_malloc_async(T** p, size_t bytes, cudaStream_t s) {
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
+    return cudaMallocAsync(reinterpret_cast<void**>(p), bytes, s);
+}
+template <typename T>
+inline cudaError_t gz_malloc_host(T** p, size_t bytes) {
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
+    return cudaMallocHost(reinterpret_cast<void**>(p), bytes);
+}
+
+// Raises a kernel's dynamic shared-memory limit on the current device, once per
+// device (the attribute is per device; devices past 64 set it on every call).
+// `done` is the kernel's own bitmask of devices already set.
+template <typename K>
+inline cudaError_t smem_attr_once(K* kernel, int bytes, std::atomic<unsigned long long>& done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+    return e;
+}
+
 void set_error(const char* fmt, ...);
 gz_status cuda_fail(cudaError_t e, const char* what);
 
@@ -144,20 +179,28 @@ struct Query {
     int out_slot = -1;         // count slot in the launch's count array (-1: its index)
 };
 struct LaunchCfg {
-    int block_warps = 8;  // warps per CTA
-    int chunk = 4;        // work units per queue pop
-    int blocks = 0;       // 0 = auto (resident CTAs on every SM)
+    int block_warps = 8;     // warps per CTA
+    int chunk = 4;           // work units per queue pop
+    int blocks = 0;          // 0 = auto (resident CTAs on every SM)
+    int64_t split_min = 512;   // loop-2 candidates from which a unit goes to the split pass
+    int64_t split_chunk = 256; // loop-2 candidates per split-pass work item
 };
 uint64_t scratch_words_per_warp(const GzProg& p, const gz_graph& g, const GzView& v);
+// Device bytes count_launch needs beside the scratch (descriptors, counters,
+// deferred records).
+uint64_t launch_meta_bytes(const Query* qs, int nq);
 gz_status count_launch(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream_t s,
                        unsigned long long* d_counts, void* scratch, uint64_t scratch_bytes,
-                       int* d_status);
+                       int* d_status, void* meta, uint64_t meta_bytes);
 int resident_warps(const LaunchCfg& cfg);
 
 // Bytes of counters (queue, count, status) at the start of a count region.
 constexpr uint64_t kRegionHeader = 256;
+// Bytes of a single-query region before its scratch (counters, and with split
+// the deferred records of the second pass).
+uint64_t one_meta_bytes(const Query& Q, bool split);
 gz_status count_one_in_region(const Query& Q, const LaunchCfg& cfg, cudaStream_t s, void* region,
-                              uint64_t scratch_bytes, uint64_t* out_count);
+                              uint64_t scratch_bytes, bool split, uint64_t* out_count);
 
 // clique side (gz_clique.cu): oriented k-cliques as bitsets over the root's out-list
 constexpr int kCliqueMaxOut = 1024;   // largest out-list whose rows fit in shared memory
@@ -166,14 +209,17 @@ bool clique_eligible(const GzProg& p, const gz_plan& plan, const GzView& v);
 // Enqueues nq queries on stream s: oriented cliques on the bitset kernels (their
 // roots with out-lists longer than kCliqueLongOut on the general kernel), the rest
 // in one persistent general launch. Query i adds its count to d_counts[i];
-// d_work holds 3 zeroed counters per query; scratch as for count_launch. With
-// overlap, a mix of queries forks onto a per-device stream pool and joins s
-// again (the server passes false: its slots already overlap on their own streams).
+// d_work holds 3 zeroed counters per query; scratch as for count_launch; meta
+// holds mixed_meta_bytes(qs, nq) bytes for the general launch. With overlap, a
+// mix of queries forks onto a per-device stream pool and joins s again (the
+// server passes false: its slots already overlap on their own streams).
 gz_status launch_mixed(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream_t s,
                        unsigned long long* d_counts, int* d_status, unsigned long long* d_work,
-                       void* scratch, uint64_t scratch_bytes, bool overlap);
-// Scratch bytes launch_mixed needs for these queries.
+                       void* scratch, uint64_t scratch_bytes, void* meta, uint64_t meta_bytes,
+                       bool overlap);
+// Scratch and metadata bytes launch_mixed needs for these queries.
 uint64_t mixed_scratch_bytes(const Query* qs, int nq, const LaunchCfg& cfg);
+uint64_t mixed_meta_bytes(const Query* qs, int nq);
 gz_status clique_prepare(const GzView& v, int64_t n, cudaStream_t s);
 gz_status clique_launch(int k, const GzView& v, int64_t n, int64_t lo, int64_t hi, cudaStream_t s,
                         unsigned long long* d_count, unsigned long long* d_work);

@@ -1,16 +1,16 @@
 // gz_noalloc.cu - gz_count_noalloc: pattern counting without any device
-// allocation, for callers that must not call cudaMalloc at counting time: code
-// running while a stream is being captured into a CUDA graph, real-time loops
-// that forbid allocator calls after start-up, and hosts whose memory manager
-// owns the whole device. The paper has no counterpart; this is a deployment
-// variant of the general enumeration kernel.
+// allocation, for callers that must not allocate at counting time: real-time
+// loops that forbid allocator calls after start-up, and host applications whose
+// own memory manager reserves the whole device. The paper has no counterpart;
+// this is a deployment variant of the general enumeration kernel.
 //
 // All device state of a call (queue counter, count, status and the per-warp
 // set-operation scratch) lives in one file-scope static device array of fixed
 // size, loaded with the library and held by every GPU that uses it until the
 // process exits. Every call reuses that array: calls whose kernels overlap on
 // the GPU (on different streams, or from several host threads) race on it and
-// must be serialised by the caller.
+// must be serialised by the caller. The array's device address is looked up
+// once per device and kept, so it goes stale if the device is reset.
 #include <mutex>
 
 #include "gz_internal.h"
@@ -78,6 +78,6 @@ extern "C" gz_status gz_count_noalloc(const gz_plan* p, const gz_graph* g, int u
     LaunchCfg cfg;
     cfg.block_warps = 8;
     cfg.chunk = 4;
-    return count_one_in_region(q, cfg, (cudaStream_t)stream, region, GZ_NOALLOC_SCRATCH_BYTES,
+    return count_one_in_region(q, cfg, (cudaStream_t)stream, region, GZ_NOALLOC_SCRATCH_BYTES, false,
                                out_count);
 }

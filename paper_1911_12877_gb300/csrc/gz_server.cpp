@@ -108,13 +108,14 @@ gz_status launch_batch(gz_server* s, Slot& sl) {
         gz_status st = prepare_query(r->plan, r->graph, r->ori, 0, -1, sl.stream, qs[i]);
         if (st != GZ_OK) return st;
     }
-    const uint64_t need = mixed_scratch_bytes(qs.data(), nq, kCfg) + 256;
+    const uint64_t meta = (mixed_meta_bytes(qs.data(), nq) + 255) & ~255ull;
+    const uint64_t need = meta + mixed_scratch_bytes(qs.data(), nq, kCfg) + 256;
     // counts [nq], status, clique work counters [3 nq]
     const size_t words = (size_t)nq + 1 + 3 * (size_t)nq;
     void* scratch = nullptr;
     unsigned long long* d = nullptr;
-    cudaError_t e = cudaMallocAsync(&scratch, need, sl.stream);
-    if (e == cudaSuccess) e = cudaMallocAsync(&d, sizeof(unsigned long long) * words, sl.stream);
+    cudaError_t e = gz_malloc_async(&scratch, need, sl.stream);
+    if (e == cudaSuccess) e = gz_malloc_async(&d, sizeof(unsigned long long) * words, sl.stream);
     if (e != cudaSuccess) {
         if (scratch) cudaFreeAsync(scratch, sl.stream);
         return cuda_fail(e, "server: scratch");
@@ -123,7 +124,7 @@ gz_status launch_batch(gz_server* s, Slot& sl) {
     gz_status st = e == cudaSuccess ? GZ_OK : cuda_fail(e, "server: memset");
     if (st == GZ_OK)
         st = launch_mixed(qs.data(), nq, kCfg, sl.stream, d, reinterpret_cast<int*>(d + nq), d + nq + 1,
-                          scratch, need, false);
+                          reinterpret_cast<char*>(scratch) + meta, need - meta, scratch, meta, false);
     if (st == GZ_OK) {
         e = cudaMemcpyAsync(sl.h_counts, d, sizeof(unsigned long long) * (nq + 1), cudaMemcpyDeviceToHost, sl.stream);
         if (e != cudaSuccess) st = cuda_fail(e, "server: copy back");
@@ -250,7 +251,7 @@ gz_status gz_server_create(const gz_server_opts* opts, gz_server** out) {
         sl.cap = s->opts.max_batch;
         cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done_ev, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaMallocHost(&sl.h_counts, sizeof(unsigned long long) * (sl.cap + 1));
+        if (e == cudaSuccess) e = gz_malloc_host(&sl.h_counts, sizeof(unsigned long long) * (sl.cap + 1));
         if (e != cudaSuccess) {
             gz_status st = cuda_fail(e, "gz_server_create");
             gz_server_destroy(s);

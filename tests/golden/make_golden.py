@@ -82,6 +82,25 @@ def clique_k5_full():
     _dump("clique_rmat20.json", rec)
 
 
+def clique_work():
+    """The 32-bit word operations of the per-root bitset form of the K4 and K5
+    loops on the k-clique workload (oracle.clique_bitset_work), merged into
+    clique_rmat20.json; the walk's clique counts must equal the stored ones."""
+    g = S.rmat_clique()
+    go, _ = O.reindex(g)
+    path = os.path.join(HERE, "clique_rmat20.json")
+    rec = json.load(open(path))
+    assert rec["nnz"] == g.nnz
+    for name, k in (("k4", 4), ("k5", 5)):
+        t = time.time()
+        c, w = O.clique_bitset_work(k, go)
+        assert c == rec[name]["count"], (name, c)
+        rec[name]["bitset_words"] = w
+        rec[name]["bitset_words_s"] = round(time.time() - t, 1)
+        print(name, w, rec[name]["bitset_words_s"], flush=True)
+    _dump("clique_rmat20.json", rec)
+
+
 # Root ranges (reindexed ids) of the arbitrary-pattern workload, from hub blocks
 # down to low-degree blocks. Each range starts at width 1 and doubles while one
 # oracle run stays under SAMPLE_S seconds; a run that passes ATTEMPT_S is
@@ -102,9 +121,10 @@ class _Worker:
     so one that runs past ATTEMPT_S can be stopped (OpenMP state does not
     survive a fork, hence spawn and a graph file instead of inheritance)."""
 
-    def __init__(self, path):
+    def __init__(self, path, attempt_s=None):
         import multiprocessing as mp
         self.path = path
+        self.attempt_s = ATTEMPT_S if attempt_s is None else attempt_s
         self.ctx = mp.get_context("spawn")
         self._start()
 
@@ -113,9 +133,9 @@ class _Worker:
         self.proc = self.ctx.Process(target=_worker_main, args=(child, self.path), daemon=True)
         self.proc.start()
 
-    def count(self, a, order, lo, hi):
+    def count(self, a, order, lo, hi, timeout=None):
         self.parent.send((a, order, lo, hi))
-        if self.parent.poll(ATTEMPT_S):
+        if self.parent.poll(self.attempt_s if timeout is None else timeout):
             return self.parent.recv()
         self.proc.kill()
         self.proc.join()
@@ -137,6 +157,30 @@ def _worker_main(conn, path):
         conn.send((int(c), int(e)))
 
 
+def _samples(worker, a, order, starts, n=None):
+    """[lo, hi, count, E] per start: the width doubles from 1 while one oracle run
+    stays under SAMPLE_S (a run past the worker's limit keeps the previous width)."""
+    samples = []
+    for s in starts:
+        if n is not None and s >= n:
+            continue
+        w, last = 1, None
+        while w <= PATTERN_MAX_W:
+            hi = s + w if n is None else min(n, s + w)
+            t = time.time()
+            r = worker.count(a, order, s, hi)
+            dt = time.time() - t
+            if r is None:
+                break
+            last = [s, hi, r[0], r[1]]
+            if dt > SAMPLE_S or (n is not None and hi >= n):
+                break
+            w *= 2
+        if last is not None:
+            samples.append(last)
+    return samples
+
+
 def patterns(names=None):
     """Recomputes the samples of `names` (default: all five) and keeps the other
     patterns' stored records."""
@@ -156,27 +200,94 @@ def patterns(names=None):
     for name in (names or PATTERN_SET):
         a, order = _plan(name)
         t0 = time.time()
-        samples = []
-        for s in PATTERN_STARTS_BY_NAME.get(name, PATTERN_STARTS):
-            w, last = 1, None
-            while w <= PATTERN_MAX_W:
-                t = time.time()
-                r = worker.count(a, order, s, s + w)
-                dt = time.time() - t
-                if r is None:
-                    break
-                last = [s, s + w, r[0], r[1]]
-                if dt > SAMPLE_S:
-                    break
-                w *= 2
-            if last is not None:
-                samples.append(last)
+        samples = _samples(worker, a, order, PATTERN_STARTS_BY_NAME.get(name, PATTERN_STARTS))
         rec["patterns"][name] = {"order": order, "samples": samples,
                                  "oracle_s": round(time.time() - t0, 1)}
         print(name, rec["patterns"][name], flush=True)
     worker.close()
     os.remove(tmp)
     _dump("patterns_rmat22.json", rec)
+
+
+# The batched workload: 64 queries over 16 R-MAT graphs (synthetic.patterns.
+# batch_queries). Each distinct (graph, pattern) pair gets the oracle's full count
+# when it finishes within BATCH_FULL_S on the host; otherwise root-range samples
+# (reindexed ids) from hub blocks to low-degree blocks, as for R-MAT 22. The file
+# is written after every pair, and a rerun keeps the pairs already stored.
+BATCH_FULL_S = 1500.0
+BATCH_SAMPLE_FRACS = [0.0, 0.001, 0.01, 0.05, 0.2, 0.5]
+
+
+def _graph_worker(g, attempt_s):
+    import numpy as np
+    import tempfile
+    go, _ = O.reindex(g)
+    tmp = os.path.join(tempfile.mkdtemp(), "go.npz")
+    np.savez(tmp, n=go.n, row_ptr=go.row_ptr, col=go.col)
+    return _Worker(tmp, attempt_s), tmp
+
+
+def batched():
+    from synthetic.patterns import batch_queries
+    table = batch_queries()
+    path = os.path.join(HERE, "batched_table.json")
+    rec = {"queries": [[gi, name] for gi, name in table], "oriented": True, "graphs": {},
+           "results": {}}
+    if os.path.exists(path):
+        old = json.load(open(path))
+        if old.get("queries") == rec["queries"]:
+            rec["graphs"], rec["results"] = old["graphs"], old["results"]
+    for gi in sorted({gi for gi, _ in table}):
+        g = S.batch_graph(gi)
+        names = sorted({n for gj, n in table if gj == gi})
+        old = rec["graphs"].get(str(gi))
+        if old and old["nnz"] == g.nnz and all(f"{gi}:{n}" in rec["results"] for n in names):
+            continue
+        rec["graphs"][str(gi)] = {"name": g.name, "n": g.n, "nnz": g.nnz}
+        worker, tmp = _graph_worker(g, ATTEMPT_S)
+        for name in names:
+            key = f"{gi}:{name}"
+            if key in rec["results"]:
+                continue
+            a, order = _plan(name)
+            t = time.time()
+            r = worker.count(a, order, 0, g.n, timeout=BATCH_FULL_S)
+            if r is not None:
+                res = {"order": order, "count": r[0], "elems": r[1],
+                       "oracle_s": round(time.time() - t, 1)}
+            else:
+                starts = [int(f * g.n) for f in BATCH_SAMPLE_FRACS]
+                res = {"order": order, "full_count_over_s": BATCH_FULL_S,
+                       "samples": _samples(worker, a, order, starts, g.n),
+                       "oracle_s": round(time.time() - t, 1)}
+            rec["results"][key] = res
+            print(key, g.name, res, flush=True)
+            _dump("batched_table.json", rec)
+        worker.close()
+        os.remove(tmp)
+    _dump("batched_table.json", rec)
+
+
+# The served workload's graph, R-MAT 24 (ef 16, seed 24): full counts are out of
+# reach for the oracle, so every pattern of the request mix gets root-range
+# samples over the reindexed ids, hub blocks down to low-degree blocks.
+SERVED_STARTS = [64, 2000, 50000, 400000, 2000000, 6000000]
+
+
+def served():
+    from synthetic.patterns import SERVED_PATTERNS
+    g = S.rmat_served()
+    worker, tmp = _graph_worker(g, ATTEMPT_S)
+    rec = {"graph": g.name, "n": g.n, "nnz": g.nnz, "oriented": True, "patterns": {}}
+    for name in SERVED_PATTERNS:
+        a, order = _plan(name)
+        t0 = time.time()
+        rec["patterns"][name] = {"order": order, "samples": _samples(worker, a, order, SERVED_STARTS),
+                                 "oracle_s": round(time.time() - t0, 1)}
+        print(name, rec["patterns"][name], flush=True)
+        _dump("served_rmat24.json", rec)
+    worker.close()
+    os.remove(tmp)
 
 
 if __name__ == "__main__":

@@ -179,12 +179,44 @@ def test_batch_equals_alone():
             assert c == oracle_count(name, idx[id(G)])
 
 
+def test_batched_table_against_oracle():
+    """The batched workload (64 queries over 16 R-MAT graphs) in one gz_count_batch
+    call against the oracle's values stored by tests/golden/make_golden.py: full
+    counts where the oracle finished, else its sampled root ranges (each counted
+    here through gz_count_ex) plus equality with the query counted alone."""
+    gold = json.load(open(os.path.join(GOLDEN, "batched_table.json")))
+    from synthetic.patterns import batch_queries
+    table = batch_queries()
+    assert gold["queries"] == [[gi, n] for gi, n in table]
+    graphs = {}
+    for gi in sorted({gi for gi, _ in table}):
+        g = S.batch_graph(gi)
+        assert gold["graphs"][str(gi)]["nnz"] == g.nnz
+        graphs[gi] = gz.Graph.from_csr(g).orient()
+    plans = {n: gz.Plan(n) for n in {n for _, n in table}}
+    got = gz.count_batch([plans[n] for _, n in table], [graphs[gi] for gi, _ in table], [True] * len(table))
+    sampled = 0
+    for (gi, n), c in zip(table, got):
+        r = gold["results"][f"{gi}:{n}"]
+        assert r["order"] == plans[n].info()["order"] or "count" in r
+        if "count" in r:
+            assert c == r["count"], (gi, n, c, r["count"])
+        else:
+            sampled += 1
+            assert c == gz.count(plans[n], graphs[gi], True), (gi, n)
+            for lo, hi, want, _ in r["samples"]:
+                assert gz.count(plans[n], graphs[gi], True, lo, hi) == want, (gi, n, lo, hi)
+    assert sampled <= len(table) // 4
+
+
 def test_server_equals_alone():
     g = S.rmat(12, 16, 50)
     G = gz.Graph.from_csr(g).orient()
     names = ["triangle", "c4", "diamond", "k4", "k5", "chordal5"]
     plans = [gz.Plan(n) for n in names]
     alone = [gz.count(p, G, True) for p in plans]
+    # served, FIFO and alone must all equal the oracle's count for each pattern
+    assert alone == [oracle_count(n, g) for n in names]
     srv = gz.Server(max_inflight=3, max_batch=8)
     rng = np.random.default_rng(5)
     pidx = rng.integers(0, len(names), 60).astype(np.int32)

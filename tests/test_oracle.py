@@ -148,6 +148,49 @@ def test_cost_model_prefers_triangle_first_for_tailed_triangle():
     assert c == pytest.approx(min(O.cost(a, s) for s in O.distinct_schedules(a)))
 
 
+def _paw_costs_by_hand():
+    """The Sec. 5.4 model for the two tailed-triangle schedules of Sec. 5.1, written
+    out by hand in exact rationals (n = 1000 vertices, p = 5/999 from Sec. 7.3).
+
+    Labels: C = 0, D = 1 (the triangle corners without the tail), B = 2 (the
+    corner with the tail), A = 3 (the tail). Aut = {id, (C D)}, so each schedule
+    keeps one restriction id(D) < id(C).
+
+    [C, D, B, A]: loop iterations n; n p (D ~ C); n p^2 (B ~ C, D);
+    n p (1-p)^2 (A ~ B only). The restriction binds D under C from loop 1 on,
+    so loops 1..3 pass it with probability 1/2 (Appendix: prod 1/z_i, z_C = 2).
+
+    [A, B, C, D]: loop iterations n; n p (B ~ A); n p (1-p) (C ~ B, not A);
+    n p^2 (1-p) (D ~ B, C, not A). The restriction binds D under C in loop 3
+    only, passed with probability 1/2.
+
+    Cost = sum over loops of (product of iterations down to that loop) x the
+    restriction pass probability of that loop."""
+    from fractions import Fraction as Fr
+    n, p = Fr(1000), Fr(5, 999)
+    q = 1 - p
+    h = Fr(1, 2)
+    l1, l2, l3 = n * p, n * p ** 2, n * p * q ** 2
+    cdba = n + n * l1 * h + n * l1 * l2 * h + n * l1 * l2 * l3 * h
+    m1, m2, m3 = n * p, n * p * q, n * p ** 2 * q
+    abcd = n + n * m1 + n * m1 * m2 + n * m1 * m2 * m3 * h
+    return float(cdba), float(abcd)
+
+
+PAW_C, PAW_D, PAW_B, PAW_A = 0, 1, 2, 3
+
+
+def test_cost_model_closed_form_tailed_triangle():
+    a = adjacency("paw")
+    cdba, abcd = _paw_costs_by_hand()
+    s1, s2 = [PAW_C, PAW_D, PAW_B, PAW_A], [PAW_A, PAW_B, PAW_C, PAW_D]
+    assert list(O.restrictions(a, s1)[0]) == [-1, 0, -1, -1]
+    assert list(O.restrictions(a, s2)[0]) == [-1, -1, -1, 2]
+    assert O.cost(a, s1) == pytest.approx(cdba, rel=1e-12)
+    assert O.cost(a, s2) == pytest.approx(abcd, rel=1e-12)
+    assert cdba < abcd  # Sec. 5.1: the triangle-first schedule is the better one
+
+
 # ------------------------------------------------------------------ Oracle A closed forms
 
 @pytest.mark.parametrize("k", [2, 3, 4, 5, 6])
@@ -316,6 +359,7 @@ def _pins_pass():
         test_reindex_orders_by_degree(1)
         for k in SCHEDULE_TABLE:
             test_schedule_counts(k)
+        test_cost_model_closed_form_tailed_triangle()
     except AssertionError:
         return False
     return True
@@ -352,3 +396,44 @@ def test_motif_patterns_are_connected_and_distinct():
         for a in pats:
             assert (a == a.T).all() and not a.diagonal().any()
             assert len(O.automorphisms(a)) >= 1  # the oracle accepts it as a connected pattern
+
+
+# ------------------------------------------------------------------ bitset work measure
+
+def _bitset_work_brute(k, g):
+    """Word operations of the per-root bitset clique walk, by plain enumeration:
+    every chain of out-list indices a > b > ... (2 to k-2 of them, pairwise
+    adjacent in the graph) builds one set whose last index lim bounds it, and
+    that set spans ceil(lim / 32) words. Also counts the k-cliques."""
+    words = cnt = 0
+    for v in range(g.n):
+        out = [int(u) for u in g.neighbors(v) if u < v]
+        if len(out) < k - 1:
+            continue
+        nb = [set(int(x) for x in g.neighbors(u)) for u in out]
+
+        def chains(ch):
+            nonlocal words, cnt
+            if len(ch) == k - 1:  # a k-clique: one bit of the last loop's set
+                cnt += 1
+                return
+            if len(ch) >= 2:  # a chain of 2 .. k-2 indices builds one set
+                words += (ch[-1] + 31) // 32
+            for c in range(ch[-1]):
+                if all(out[c] in nb[x] for x in ch):
+                    chains(ch + [c])
+        for a in range(len(out)):
+            chains([a])
+    return cnt, words
+
+
+@pytest.mark.parametrize("k", [4, 5, 6])
+def test_clique_bitset_work_matches_brute_definition(k):
+    import math
+    for g in (S.complete(40), S.random_small(70, 0.45, 31), S.rmat(8, 16, 3)):
+        go, _ = O.reindex(g)
+        cnt, words = O.clique_bitset_work(k, go)
+        bc, bw = _bitset_work_brute(k, go)
+        assert (cnt, words) == (bc, bw), (g.name, k)
+        if g.name == "K40":
+            assert cnt == math.comb(40, k)

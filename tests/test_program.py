@@ -43,6 +43,17 @@ def test_planner_matches_oracle_planner(name):
     assert (gz.schedules(a) == O.distinct_schedules(a)).all()
 
 
+def test_planner_cost_matches_hand_derived_model():
+    # the library's Sec. 5.4 model against the closed forms written out by hand
+    # (not the oracle's code) for the two Sec. 5.1 tailed-triangle schedules
+    from test_oracle import PAW_A, PAW_B, PAW_C, PAW_D, _paw_costs_by_hand
+    a = adjacency("paw")
+    cdba, abcd = _paw_costs_by_hand()
+    for order, want in (([PAW_C, PAW_D, PAW_B, PAW_A], cdba), ([PAW_A, PAW_B, PAW_C, PAW_D], abcd)):
+        assert gz.Plan(a, order=order).info()["est_cost"] == pytest.approx(want, rel=1e-12)
+    assert gz.Plan(a).info()["est_cost"] <= cdba
+
+
 def test_named_patterns_match_inputs():
     for name in EDGES:
         if name == "asym6":
