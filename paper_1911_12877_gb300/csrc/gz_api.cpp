@@ -489,7 +489,7 @@ void gz_graph_destroy(gz_graph* g) {
     auto free_view = [](GzView& v, bool csr) {
         if (csr) { cudaFree(v.rp); cudaFree(v.col); }
         cudaFree(v.dag_rp); cudaFree(v.dag_col); cudaFree(v.dag_src); cudaFree(v.src);
-        cudaFree(v.heavy_rows);
+        cudaFree(v.heavy_rows); cudaFree(v.slot_dev);
     };
     cudaDeviceSynchronize();
     free_view(g->orig, g->orig.owned_csr);

@@ -12,11 +12,15 @@
 //
 //  - k_clique_small: one warp per root with |O| <= 32 (one 32-bit row per lane's
 //    vertex, rows in shared memory).
-//  - k_clique_big: one 512-thread CTA per root with 32 < |O| <= kCliqueMaxOut,
-//    rows in shared memory (odd word stride), then the (a, b) edges of the
-//    local DAG spread over all threads. Roots with |O| >= kHeavyD are split
-//    over several CTAs ("parts"); their rows are built once per out-list view
-//    by k_clique_rows into device memory and copied by each part.
+//  - k_clique_rows: the rows of every root with 32 < |O| <= kCliqueMaxOut,
+//    built once per out-list view into device memory and kept there; the
+//    kernels below copy them into shared memory.
+//  - k_clique_warp (K = 4, 5): one 512-thread CTA per root, its warps taking
+//    the rows a of the root dynamically and the pairs (a, b) one per lane.
+//  - k_clique_big (K >= 6): one 512-thread CTA per root or per part of a root
+//    (roots with |O| >= kSplitD are split over several CTAs), rows in shared
+//    memory with an odd word stride, the (a, b) edges of the local DAG spread
+//    over all threads.
 //  - k_clique_long: roots with kCliqueMaxOut < |O| <= kCliqueLongOut, rows in
 //    device memory (k_clique_long_rows); longer roots are left to the caller.
 #include <algorithm>
@@ -35,9 +39,20 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kThreads = 256;
 constexpr int kBigPop = 16;     // roots per queue slot of the big kernel; most are skipped
 constexpr int kBigThreads = 512;  // threads of a big-kernel CTA (one root at a time)
-constexpr int kHeavyD = 128;    // out-degree from which a root is split over several CTAs
+constexpr int kHeavyD = 33;     // out-degree from which a root's rows are built once and cached
+constexpr int kSplitD = 128;    // out-degree from which k_clique_big splits a root over several CTAs
 constexpr uint64_t kHeavyRowWords = 1ull << 29;  // budget for prebuilt heavy rows (2 GiB)
 constexpr uint64_t kLongRowWords = 1ull << 30;   // budget for long roots' global rows (4 GiB)
+
+// Row stride (32-bit words) of the bitset rows of a root with d out-neighbours,
+// kept in shared memory and in the prebuilt heavy rows: ceil(d / 32) words
+// rounded up to whole 16-byte chunks, with an odd chunk count, so rows start on
+// 16-byte boundaries (128-bit loads) and the same chunk of consecutive rows
+// falls in different bank groups.
+__host__ __device__ __forceinline__ int row_stride(int d) {
+    const int chunks = (((d + 31) >> 5) + 3) >> 2;
+    return (chunks | 1) << 2;
+}
 
 __device__ __forceinline__ bool has(const int32_t* __restrict__ R, int n, int32_t x) {
     int lo = 0, len = n;
@@ -204,35 +219,49 @@ __device__ __forceinline__ void build_rows(const int64_t* __restrict__ drp,
     }
 }
 
-// Rows of every heavy root, built once into global memory (one CTA per root,
-// grid-stride), so the parts of a heavy root copy them instead of rebuilding.
-// hr[i] = (root, unused, word offset of its rows in grows). Shared memory as in
-// k_clique_big (rows, O).
-__global__ void __launch_bounds__(kThreads) k_clique_rows(const int64_t* __restrict__ drp,
-                                                          const int32_t* __restrict__ dcol,
-                                                          const int4* __restrict__ hr, int nh,
-                                                          int max_out,
-                                                          uint32_t* __restrict__ grows) {
-    extern __shared__ uint32_t sm[];
-    const int Wsmax = ((max_out + 31) >> 5) | 1;
-    uint32_t* rows = sm;
-    int32_t* O = reinterpret_cast<int32_t*>(sm + (size_t)max_out * Wsmax);
-    // index of O: open-addressing hash of (vertex id << 32 | position), 2 *
-    // kCliqueMaxOut slots (load <= 1/2); 8-byte aligned after rows and O
-    const size_t hoff = ((size_t)max_out * Wsmax + max_out + 1) & ~(size_t)1;
-    unsigned long long* hx = reinterpret_cast<unsigned long long*>(sm + hoff);
+// Rows of every cached root, built once per out-list view into global memory:
+// row a of root hr[i].x goes to grows + hr[i].z + a * row_stride(d), every word
+// of it written (padding included), so the buffer needs no clearing. One CTA per
+// root at a time, roots handed out by the counter *next. O is indexed by an
+// open-addressing hash in shared memory (2 * kCliqueMaxOut slots of
+// (vertex id << 32 | position); load <= 1/2). The warps take rows a from a
+// shared counter, largest first; a warp assembles row(a) in its own small
+// shared buffer, streaming the out-list of O[a] and probing the hash (one probe
+// per entry) when that list is not much longer than a, else looking each O[b],
+// b < a, up in it by binary search, then writes the row out. Shared memory per
+// CTA stays small (hash, O, one row per warp), so many CTAs share an SM.
+constexpr int kRowsThreads = 256;
+constexpr int kRowBufWords = 36;  // >= row_stride(kCliqueMaxOut)
+static_assert(kRowBufWords >= (((kCliqueMaxOut / 32 + 3) / 4) | 1) * 4, "row buffer too small");
+
+__global__ void __launch_bounds__(kRowsThreads) k_clique_rows(const int64_t* __restrict__ drp,
+                                                              const int32_t* __restrict__ dcol,
+                                                              const int4* __restrict__ hr, int nh,
+                                                              unsigned long long* __restrict__ next,
+                                                              uint32_t* __restrict__ grows) {
+    __shared__ unsigned long long hx[2 * kCliqueMaxOut];
+    __shared__ int32_t O[kCliqueMaxOut];
+    __shared__ uint32_t rbuf_s[kRowsThreads / 32][kRowBufWords];
+    __shared__ int s_h, s_next;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int32_t* stage = reinterpret_cast<int32_t*>(hx + 2 * kCliqueMaxOut) + (size_t)warp * kCliqueMaxOut;
+    uint32_t* rbuf = rbuf_s[warp];
     constexpr unsigned kMask = 2 * kCliqueMaxOut - 1;
-    for (int h = blockIdx.x; h < nh; h += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_h = (int)atomicAdd(next, 1ull);
+            s_next = 0;
+        }
+        __syncthreads();
+        const int h = s_h;
+        if (h >= nh) break;
         const int64_t v = hr[h].x;
         const int64_t ob = drp[v];
         const int d = (int)(drp[v + 1] - ob);
-        const int Ws = ((d + 31) >> 5) | 1;
-        for (int i = threadIdx.x; i < 2 * kCliqueMaxOut; i += kThreads) hx[i] = ~0ull;
-        for (int i = threadIdx.x; i < d * Ws; i += kThreads) rows[i] = 0;
+        const int Ws = row_stride(d);
+        uint32_t* dst = grows + (uint32_t)hr[h].z;
+        for (int i = threadIdx.x; i < 2 * kCliqueMaxOut; i += kRowsThreads) hx[i] = ~0ull;
         __syncthreads();
-        for (int i = threadIdx.x; i < d; i += kThreads) {
+        for (int i = threadIdx.x; i < d; i += kRowsThreads) {
             const int32_t x = dcol[ob + i];
             O[i] = x;
             const unsigned long long kv = ((unsigned long long)(uint32_t)x << 32) | (uint32_t)i;
@@ -240,15 +269,18 @@ __global__ void __launch_bounds__(kThreads) k_clique_rows(const int64_t* __restr
             while (atomicCAS(&hx[sl], ~0ull, kv) != ~0ull) sl = (sl + 1) & kMask;
         }
         __syncthreads();
-        // row(a): stream N'(O[a]) and look each entry up in the index of O (one
-        // probe instead of a binary search) when it is not much longer than a;
-        // else stage it and binary-search it for each O[b], b < a
-        for (int a = warp + 1; a < d; a += kThreads / 32) {
+        for (;;) {
+            int m = 0;
+            if (lane == 0) m = atomicAdd(&s_next, 1);
+            m = __shfl_sync(kFull, m, 0);
+            const int a = d - 1 - m;
+            if (a < 0) break;
+            for (int w = lane; w < Ws; w += 32) rbuf[w] = 0u;
+            __syncwarp();
             const int32_t u = O[a];
             const int64_t ub = drp[u];
             const int du = (int)(drp[u + 1] - ub);
-            uint32_t* ra = rows + (size_t)a * Ws;
-            if (du <= 4 * a || du > kCliqueMaxOut) {
+            if (du <= 4 * a) {
                 for (int i = lane; i < du; i += 32) {
                     const int32_t x = __ldg(dcol + ub + i);
                     unsigned sl = ((uint32_t)x * 0x9E3779B1u) >> 21;
@@ -259,23 +291,20 @@ __global__ void __launch_bounds__(kThreads) k_clique_rows(const int64_t* __restr
                         if ((int32_t)(e >> 32) == x) { b = (int)(uint32_t)e; break; }
                         sl = (sl + 1) & kMask;
                     }
-                    if (b >= 0 && b < a) atomicOr(ra + (b >> 5), 1u << (b & 31));
+                    if (b >= 0 && b < a) atomicOr(rbuf + (b >> 5), 1u << (b & 31));
                 }
             } else {
-                for (int i = lane; i < du; i += 32) stage[i] = __ldg(dcol + ub + i);
-                __syncwarp();
                 for (int b0 = 0; b0 < a; b0 += 32) {
                     const int b = b0 + lane;
-                    const bool in = b < a && index_of(stage, du, O[b]) >= 0;
-                    const uint32_t m = __ballot_sync(kFull, in);
-                    if (lane == 0) ra[b0 >> 5] = m;
+                    const bool in = b < a && has(dcol + ub, du, O[b]);
+                    const uint32_t msk = __ballot_sync(kFull, in);
+                    if (lane == 0) rbuf[b0 >> 5] = msk;
                 }
-                __syncwarp();
             }
+            __syncwarp();
+            for (int w = lane; w < Ws; w += 32) dst[(size_t)a * Ws + w] = rbuf[w];
+            __syncwarp();
         }
-        __syncthreads();
-        uint32_t* dst = grows + (uint32_t)hr[h].z;
-        for (int i = threadIdx.x; i < d * Ws; i += kThreads) dst[i] = rows[i];
         __syncthreads();
     }
 }
@@ -283,7 +312,8 @@ __global__ void __launch_bounds__(kThreads) k_clique_rows(const int64_t* __restr
 // Roots with 32 < |O| <= max_out: one CTA per root, or per part of a heavy
 // root. Shared memory: rows [max_out * Wsmax] words (row stride Ws = W | 1 for
 // the current root, odd so that threads reading word w of different rows hit
-// different banks), O [max_out], pre [max_out + 1].
+// different banks; prebuilt rows, stored with row_stride(d), are re-strided on
+// the copy), O [max_out], pre [max_out + 1].
 //
 // Rows come from build_rows or, for a part of a heavy root, are copied from the
 // rows k_clique_rows built once for that root. pre[a] counts the local DAG
@@ -344,7 +374,11 @@ __global__ void __launch_bounds__(kBigThreads) k_clique_big(const int64_t* __res
         const int Ws = ((d + 31) >> 5) | 1;
         for (int i = threadIdx.x; i < d; i += kBigThreads) O[i] = dcol[ob + i];
         if (src) {
-            for (int i = threadIdx.x; i < d * Ws; i += kBigThreads) rows[i] = __ldg(src + i);
+            const int Wg = row_stride(d);
+            for (int i = threadIdx.x; i < d * Ws; i += kBigThreads) {
+                const int a = i / Ws, w = i - a * Ws;
+                rows[i] = w < Wg ? __ldg(src + (size_t)a * Wg + w) : 0u;
+            }
             __syncthreads();
         } else {
             for (int i = threadIdx.x; i < d * Ws; i += kBigThreads) rows[i] = 0;
@@ -398,6 +432,229 @@ __global__ void __launch_bounds__(kBigThreads) k_clique_big(const int64_t* __res
         }
         __syncthreads();
       }
+    }
+    unsigned long long s = block_sum(acc, red);
+    if (threadIdx.x == 0 && s) atomicAdd(count, s);
+}
+
+// K = 4 and K = 5 on roots with 32 < |O| <= max_out: k_clique_warp. The rows
+// sit in shared memory as in k_clique_big, but the work is spread by warps, not
+// by CTA-wide pair indices. One CTA takes one root at a time (heavy roots
+// first, heaviest first, with their prebuilt rows; no root is split over CTAs:
+// on the skewed graphs measured the largest root holds a fifth of one SM's
+// share of the work). The CTA's warps pop the root's rows a from a counter in
+// shared memory, largest a first; for its row a, a warp walks the pairs
+// (a, b in row(a)) 32 at a time, one pair per lane. For K = 5 a lane finds its
+// b from the popcount prefix of row(a)'s words (one word per lane, computed once
+// per row) by a shuffle search; for K = 4, whose pairs are cheap, lane l simply
+// takes bit l of each word of row(a). Then the lane counts its pair:
+//  - K = 4: |row(a) & row(b)| below b;
+//  - K = 5: with S = row(a) & row(b) (bits below b) held in registers, the sum
+//    over c in S of |S & row(c)|, row(c) holding bits below c only.
+// Rows are read as 16-byte chunks (row_stride keeps them aligned). Warps never
+// wait for each other inside a root.
+constexpr int kWarpCta = 512;
+constexpr int kWarpCtaWarps = kWarpCta / 32;
+
+// Position of the k-th set bit (0-based) of m; requires k < popc(m).
+__device__ __forceinline__ int select_bit(uint32_t m, int k) {
+    int pos = 0;
+    int c = __popc(m & 0xffffu);
+    if (k >= c) { k -= c; m >>= 16; pos += 16; }
+    c = __popc(m & 0xffu);
+    if (k >= c) { k -= c; m >>= 8; pos += 8; }
+    c = __popc(m & 0xfu);
+    if (k >= c) { k -= c; m >>= 4; pos += 4; }
+    c = __popc(m & 0x3u);
+    if (k >= c) { k -= c; m >>= 2; pos += 2; }
+    if (k >= (int)(m & 1u)) pos += 1;
+    return pos;
+}
+
+// The popcounts run on the SM's quarter-rate XU pipe, so only words below b
+// (row(b) is zero above them) are counted.
+__device__ __forceinline__ uint32_t k4_pair(const uint4* __restrict__ rows4, int Ws4, int a, int b) {
+    const uint4* ra = rows4 + (size_t)a * Ws4;
+    const uint4* rb = rows4 + (size_t)b * Ws4;
+    const int nw = (b + 31) >> 5;
+    uint32_t cnt = 0;
+    int q = 0;
+    for (; 4 * q + 4 <= nw; ++q) {
+        const uint4 A = ra[q], B = rb[q];
+        cnt += __popc(A.x & B.x) + __popc(A.y & B.y) + __popc(A.z & B.z) + __popc(A.w & B.w);
+    }
+    const int rest = nw - 4 * q;
+    if (rest > 0) {
+        const uint4 A = ra[q], B = rb[q];
+        cnt += __popc(A.x & B.x);
+        if (rest > 1) cnt += __popc(A.y & B.y);
+        if (rest > 2) cnt += __popc(A.z & B.z);
+    }
+    return cnt;
+}
+
+// WM: a multiple of 4 with WM >= ceil(b / 32); S is unrolled into WM registers.
+template <int WM>
+__device__ __forceinline__ uint32_t k5_pair(const uint4* __restrict__ rows4, int Ws4, int a, int b) {
+    const uint4* ra = rows4 + (size_t)a * Ws4;
+    const uint4* rb = rows4 + (size_t)b * Ws4;
+    const int nq = (b + 127) >> 7;
+    uint32_t S[WM];
+#pragma unroll
+    for (int q = 0; q < WM / 4; ++q) {
+        uint4 x = make_uint4(0u, 0u, 0u, 0u);
+        if (q < nq) {
+            const uint4 A = ra[q], B = rb[q];
+            x = make_uint4(A.x & B.x, A.y & B.y, A.z & B.z, A.w & B.w);
+        }
+        S[4 * q] = x.x;
+        S[4 * q + 1] = x.y;
+        S[4 * q + 2] = x.z;
+        S[4 * q + 3] = x.w;
+    }
+    // c runs over the bits of S word w (highest first, one count-leading-zeros
+    // each); row(c) is zero above word w, so exactly w + 1 words are counted
+    // (the guards are compile-time constants of the unrolled loops)
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < WM; ++w) {
+        uint32_t bits = S[w];
+        while (bits) {
+            const int hb = 31 - __clz(bits);
+            bits ^= 1u << hb;
+            const uint4* rc = rows4 + (size_t)((w << 5) + hb) * Ws4;
+#pragma unroll
+            for (int q = 0; q <= w / 4; ++q) {
+                const uint4 r = rc[q];
+                cnt += __popc(S[4 * q] & r.x);
+                if (4 * q + 1 <= w) cnt += __popc(S[4 * q + 1] & r.y);
+                if (4 * q + 2 <= w) cnt += __popc(S[4 * q + 2] & r.z);
+                if (4 * q + 3 <= w) cnt += __popc(S[4 * q + 3] & r.w);
+            }
+        }
+    }
+    return cnt;
+}
+
+template <int K>
+__device__ __forceinline__ uint32_t warp_pair(const uint4* rows4, int Ws4, int wm, int a, int b) {
+    if constexpr (K == 4) {
+        (void)wm;
+        return k4_pair(rows4, Ws4, a, b);
+    } else {
+        switch (wm) {
+            case 8: return k5_pair<8>(rows4, Ws4, a, b);
+            case 16: return k5_pair<16>(rows4, Ws4, a, b);
+            case 24: return k5_pair<24>(rows4, Ws4, a, b);
+            default: return k5_pair<32>(rows4, Ws4, a, b);
+        }
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kWarpCta, 2) k_clique_warp(const int64_t* __restrict__ drp,
+                                                          const int32_t* __restrict__ dcol,
+                                                          int64_t root_lo, int64_t root_hi,
+                                                          int max_out, int heavy_d,
+                                                          const int4* __restrict__ heavy,
+                                                          int nheavy,
+                                                          const uint32_t* __restrict__ grows,
+                                                          unsigned long long* __restrict__ work,
+                                                          unsigned long long* __restrict__ count) {
+    static_assert(K == 4 || K == 5, "k_clique_warp counts K4 and K5");
+    extern __shared__ __align__(16) uint32_t smw[];
+    __shared__ unsigned long long red[kWarpCtaWarps];
+    __shared__ int64_t s_slot;
+    __shared__ int s_next;
+    const int Wsmax = row_stride(max_out);
+    uint32_t* rows = smw;
+    int32_t* O = reinterpret_cast<int32_t*>(smw + (size_t)max_out * Wsmax);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long acc = 0;
+    const int64_t nchunks = (root_hi - root_lo + kBigPop - 1) / kBigPop;
+    for (;;) {
+        // queue slots: [0, nheavy) one heavy root each (heaviest first), then
+        // chunks of kBigPop consecutive roots (heavy ones skipped there)
+        if (threadIdx.x == 0) s_slot = (int64_t)atomicAdd(work, 1ull);
+        __syncthreads();
+        const int64_t slot = s_slot;
+        __syncthreads();
+        if (slot >= nheavy + nchunks) break;
+        int64_t v0, nr;
+        const uint32_t* src = nullptr;  // prebuilt rows of a heavy root
+        if (slot < nheavy) {
+            const int4 h = heavy[slot];
+            v0 = h.x;
+            nr = 1;
+            src = grows + (uint32_t)h.z;
+        } else {
+            v0 = root_lo + (slot - nheavy) * kBigPop;
+            nr = kBigPop;
+        }
+        for (int r = 0; r < nr; ++r) {
+            const int64_t v = v0 + r;
+            if (v >= root_hi) break;
+            const int64_t ob = drp[v];
+            const int d = (int)(drp[v + 1] - ob);
+            if (d <= 32 || d > max_out || (slot >= nheavy && d >= heavy_d)) continue;
+            const int Ws = row_stride(d);
+            if (src) {
+                const uint4* s4 = reinterpret_cast<const uint4*>(src);
+                uint4* r4 = reinterpret_cast<uint4*>(rows);
+                for (int i = threadIdx.x; i < d * (Ws >> 2); i += kWarpCta) r4[i] = __ldg(s4 + i);
+            } else {
+                for (int i = threadIdx.x; i < d; i += kWarpCta) O[i] = dcol[ob + i];
+                for (int i = threadIdx.x; i < d * Ws; i += kWarpCta) rows[i] = 0;
+                __syncthreads();
+                build_rows(drp, dcol, O, d, rows, Ws, lane, warp, kWarpCtaWarps, nullptr);
+            }
+            if (threadIdx.x == 0) s_next = 0;
+            __syncthreads();
+            const uint4* rows4 = reinterpret_cast<const uint4*>(rows);
+            const int Ws4 = Ws >> 2;
+            const int wm = ((((d + 31) >> 5) + 7) >> 3) << 3;
+            for (;;) {
+                int m = 0;
+                if (lane == 0) m = atomicAdd(&s_next, 1);
+                m = __shfl_sync(kFull, m, 0);
+                const int a = d - 1 - m;  // largest rows first
+                if (a < 1) break;
+                if constexpr (K == 4) {
+                    // rows are dense on the heavy roots: lane l takes bit l of each
+                    // word w of row(a) (b = 32 w + l), so b needs no search and all
+                    // active lanes count the same w + 1 words
+                    for (int w = 0, nwa = (a + 31) >> 5; w < nwa; ++w) {
+                        const uint32_t bits = rows[(size_t)a * Ws + w];
+                        if ((bits >> lane) & 1u) acc += k4_pair(rows4, Ws4, a, (w << 5) + lane);
+                    }
+                    continue;
+                }
+                const uint32_t word = lane < ((a + 31) >> 5) ? rows[(size_t)a * Ws + lane] : 0u;
+                int incl = __popc(word);
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                const int total = __shfl_sync(kFull, incl, 31);
+                for (int base = 0; base < total; base += 32) {
+                    const int j = base + lane;  // this lane's bit of row(a), in order
+                    int wlo = 0, whi = 31;      // first word whose inclusive count exceeds j
+#pragma unroll
+                    for (int step = 0; step < 5; ++step) {
+                        const int mid = (wlo + whi) >> 1;
+                        const int x = __shfl_sync(kFull, incl, mid);
+                        if (x > j) whi = mid; else wlo = mid + 1;
+                    }
+                    const uint32_t ww = __shfl_sync(kFull, word, wlo);
+                    const int before = __shfl_sync(kFull, incl, wlo) - __popc(ww);
+                    if (j < total) {
+                        const int b = (wlo << 5) + select_bit(ww, j - before);
+                        acc += warp_pair<K>(rows4, Ws4, wm, a, b);
+                    }
+                }
+            }
+            __syncthreads();
+        }
     }
     unsigned long long s = block_sum(acc, red);
     if (threadIdx.x == 0 && s) atomicAdd(count, s);
@@ -508,15 +765,94 @@ __global__ void __launch_bounds__(kThreads) k_clique_long(const int64_t* __restr
 }
 
 // Roots with out-degree >= kHeavyD (one pass to count, one to fill).
-__global__ void k_collect_heavy(const int64_t* __restrict__ drp, int64_t n, int heavy_d,
-                                int2* __restrict__ out, unsigned long long* __restrict__ cnt,
-                                int64_t cap) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-        const int64_t d = drp[v + 1] - drp[v];
-        if (d >= heavy_d) {
-            const unsigned long long i = atomicAdd(cnt, 1ull);
-            if (out && (int64_t)i < cap) out[i] = make_int2((int)v, (int)d);
+// Ordered collection of the roots with out-degree >= heavy_d: per-tile counts,
+// a one-CTA scan of the tile counts, then each tile writes its roots in id
+// order at its offset, so the list comes out sorted by root with no host sort.
+constexpr int kCollectThreads = 256;
+constexpr int kCollectPer = 16;  // consecutive vertices per thread
+constexpr int kCollectTile = kCollectThreads * kCollectPer;
+
+__device__ __forceinline__ int block_excl_scan(int c, int* warp_tot, int* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int x = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+        int wi = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < (int)(blockDim.x >> 5)) warp_tot[lane] = wi - x;
+        if (lane == 31) *total = wi;
+    }
+    __syncthreads();
+    return warp_tot[warp] + incl - c;
+}
+
+__global__ void __launch_bounds__(kCollectThreads) k_heavy_counts(const int64_t* __restrict__ drp, int64_t n,
+                                                                  int heavy_d, int* __restrict__ tile_cnt) {
+    __shared__ int warp_tot[kCollectThreads / 32];
+    __shared__ int total;
+    const int64_t base = (int64_t)blockIdx.x * kCollectTile + (int64_t)threadIdx.x * kCollectPer;
+    int c = 0;
+    for (int i = 0; i < kCollectPer; ++i) {
+        const int64_t v = base + i;
+        if (v < n && drp[v + 1] - drp[v] >= heavy_d) ++c;
+    }
+    block_excl_scan(c, warp_tot, &total);
+    if (threadIdx.x == 0) tile_cnt[blockIdx.x] = total;
+}
+
+// off[i] = tiles' counts before tile i, off[ntiles] = all (one CTA).
+__global__ void __launch_bounds__(1024) k_heavy_scan(const int* __restrict__ cnt, int64_t ntiles,
+                                                     int64_t* __restrict__ off) {
+    __shared__ int64_t part[1024];
+    const int64_t per = (ntiles + 1023) / 1024;
+    const int64_t b = threadIdx.x * per, e = b + per < ntiles ? b + per : ntiles;
+    int64_t sum = 0;
+    for (int64_t i = b; i < e; ++i) sum += cnt[i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t run = 0;
+        for (int i = 0; i < 1024; ++i) {
+            const int64_t x = part[i];
+            part[i] = run;
+            run += x;
+        }
+        off[ntiles] = run;
+    }
+    __syncthreads();
+    int64_t run = part[threadIdx.x];
+    for (int64_t i = b; i < e; ++i) {
+        off[i] = run;
+        run += cnt[i];
+    }
+}
+
+__global__ void __launch_bounds__(kCollectThreads) k_heavy_fill(const int64_t* __restrict__ drp, int64_t n,
+                                                                int heavy_d, const int64_t* __restrict__ off,
+                                                                int2* __restrict__ out) {
+    __shared__ int warp_tot[kCollectThreads / 32];
+    __shared__ int total;
+    const int64_t base = (int64_t)blockIdx.x * kCollectTile + (int64_t)threadIdx.x * kCollectPer;
+    int c = 0;
+    for (int i = 0; i < kCollectPer; ++i) {
+        const int64_t v = base + i;
+        if (v < n && drp[v + 1] - drp[v] >= heavy_d) ++c;
+    }
+    int64_t pos = off[blockIdx.x] + block_excl_scan(c, warp_tot, &total);
+    for (int i = 0; i < kCollectPer; ++i) {
+        const int64_t v = base + i;
+        if (v < n) {
+            const int64_t d = drp[v + 1] - drp[v];
+            if (d >= heavy_d) out[pos++] = make_int2((int)v, (int)d);
         }
     }
 }
@@ -529,46 +865,47 @@ gz_status gather_heavy(GzView& v, int64_t n, cudaStream_t s) {
         v.heavy_built = true;
         return GZ_OK;
     }
-    unsigned long long* cnt = nullptr;
-    cudaError_t e = gz_malloc_async(&cnt, sizeof(unsigned long long), s);
+    const int64_t ntiles = (n + kCollectTile - 1) / kCollectTile;
+    // tile counts | offsets [ntiles + 1]
+    const size_t cbytes = (sizeof(int) * ntiles + 15) & ~(size_t)15;
+    char* buf = nullptr;
+    cudaError_t e = gz_malloc_async(&buf, cbytes + sizeof(int64_t) * (ntiles + 1), s);
     if (e != cudaSuccess) return cuda_fail(e, "clique: heavy roots");
-    int64_t gb = (n + 255) / 256;
-    const int grid = (int)std::min<int64_t>(gb, 152 * 16);
-    unsigned long long h = 0;
-    e = cudaMemsetAsync(cnt, 0, sizeof(h), s);
-    if (e == cudaSuccess) {
-        k_collect_heavy<<<grid, 256, 0, s>>>(v.dag_rp, n, kHeavyD, nullptr, cnt, 0);
-        GZ_COUNT_LAUNCH();
-        e = cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s);
-    }
+    int* cnt = reinterpret_cast<int*>(buf);
+    int64_t* off = reinterpret_cast<int64_t*>(buf + cbytes);
+    int64_t h = 0;
+    k_heavy_counts<<<(unsigned)ntiles, kCollectThreads, 0, s>>>(v.dag_rp, n, kHeavyD, cnt);
+    GZ_COUNT_LAUNCH();
+    k_heavy_scan<<<1, 1024, 0, s>>>(cnt, ntiles, off);
+    GZ_COUNT_LAUNCH();
+    e = cudaMemcpyAsync(&h, off + ntiles, sizeof(h), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     int2* d_out = nullptr;
     std::vector<int2> tmp(h);
     if (e == cudaSuccess && h > 0) {
         e = gz_malloc_async(&d_out, sizeof(int2) * h, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s);
         if (e == cudaSuccess) {
-            k_collect_heavy<<<grid, 256, 0, s>>>(v.dag_rp, n, kHeavyD, d_out, cnt, (int64_t)h);
+            k_heavy_fill<<<(unsigned)ntiles, kCollectThreads, 0, s>>>(v.dag_rp, n, kHeavyD, off, d_out);
             GZ_COUNT_LAUNCH();
             e = cudaMemcpyAsync(tmp.data(), d_out, sizeof(int2) * h, cudaMemcpyDeviceToHost, s);
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         cudaFreeAsync(d_out, s);
     }
-    cudaFreeAsync(cnt, s);
+    cudaFreeAsync(buf, s);
     if (e != cudaSuccess) return cuda_fail(e, "clique: heavy roots");
     v.heavy.reserve(h);
     for (const int2& x : tmp) v.heavy.emplace_back(x.x, x.y);
-    std::sort(v.heavy.begin(), v.heavy.end());
     v.heavy_built = true;
     return GZ_OK;
 }
 
-// Parts a heavy root is split into: about its work (d^2 for K = 4, d^3 beyond)
-// over that of a root of out-degree kHeavyD, at most 64 and at most d. Parts
+// Parts a heavy root is split into by k_clique_big: about its work (d^2 for
+// K = 4, d^3 beyond) over that of a root of out-degree kSplitD, at most 64 and
+// at most d. Parts
 // copy the root's prebuilt rows, so a part costs little beyond its share.
 int parts_for(int K, int d) {
-    const double r = (double)d / kHeavyD;
+    const double r = (double)d / kSplitD;
     const double w = K == 4 ? r * r : r * r * r;
     const int p = (int)std::ceil(w);
     return std::max(1, std::min(std::min(p, 64), d));
@@ -581,6 +918,7 @@ int parts_for(int K, int d) {
 gz_status build_heavy_rows(GzView& v, int mo, int sms, cudaStream_t s) {
     if (v.heavy_rows_built) return GZ_OK;
     v.heavy_rows_ok = false;
+    v.slot_host.clear();
     v.heavy_off.assign(v.heavy.size(), UINT32_MAX);
     std::vector<int4> list;
     uint64_t words = 0;
@@ -589,7 +927,7 @@ gz_status build_heavy_rows(GzView& v, int mo, int sms, cudaStream_t s) {
         if (d > mo) continue;
         v.heavy_off[i] = (uint32_t)words;
         list.push_back(make_int4(v.heavy[i].first, 0, (int)words, 0));
-        words += ((uint64_t)d * (((d + 31) / 32) | 1) + 3) & ~3ull;
+        words += ((uint64_t)d * row_stride(d) + 3) & ~3ull;
     }
     v.heavy_rows_built = true;
     if (list.empty() || words > kHeavyRowWords) {
@@ -605,20 +943,23 @@ gz_status build_heavy_rows(GzView& v, int mo, int sms, cudaStream_t s) {
         e = gz_malloc(&v.heavy_rows, sizeof(uint32_t) * words);
         if (e == cudaSuccess) v.heavy_rows_cap = words;
     }
-    if (e == cudaSuccess) e = gz_malloc_async(&d_list, sizeof(int4) * list.size(), s);
+    // list | work counter
+    const size_t lbytes = (sizeof(int4) * list.size() + 15) & ~(size_t)15;
+    if (e == cudaSuccess) e = gz_malloc_async(&d_list, lbytes + 16, s);
+    unsigned long long* d_next = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(d_list) + lbytes);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_list, list.data(), sizeof(int4) * list.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_next, 0, 16, s);
     if (e == cudaSuccess) {
-        const size_t hoff = ((size_t)mo * (((mo + 31) / 32) | 1) + mo + 1) & ~(size_t)1;
-        const size_t smem = (hoff + 2 * 2 * (size_t)kCliqueMaxOut + (size_t)(kThreads / 32) * kCliqueMaxOut) * 4;
-        cudaFuncSetAttribute(k_clique_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clique_rows, kThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clique_rows, kRowsThreads, 0);
         const int rb = (int)std::min<size_t>(list.size(), (size_t)sms * std::max(1, per_sm));
-        k_clique_rows<<<rb, kThreads, smem, s>>>(v.dag_rp, v.dag_col, d_list, (int)list.size(), mo,
-                                                 v.heavy_rows);
-        GZ_COUNT_LAUNCH();
-        e = cudaGetLastError();
+        if (e == cudaSuccess) {
+            k_clique_rows<<<rb, kRowsThreads, 0, s>>>(v.dag_rp, v.dag_col, d_list, (int)list.size(), d_next,
+                                                      v.heavy_rows);
+            GZ_COUNT_LAUNCH();
+            e = cudaGetLastError();
+        }
     }
     if (d_list) cudaFreeAsync(d_list, s);
     // the rows are complete before any stream (other batch slots included) uses them
@@ -631,6 +972,34 @@ gz_status build_heavy_rows(GzView& v, int mo, int sms, cudaStream_t s) {
         return cuda_fail(e, "clique: heavy rows");
     }
     v.heavy_rows_ok = true;
+    // the heavy-root slots of k_clique_warp (one per cached root, heaviest
+    // first: a counting sort by out-degree), kept on the device for counts over
+    // all roots and on the host for root ranges
+    std::vector<int> start(mo + 2, 0);
+    for (size_t i = 0; i < v.heavy.size(); ++i)
+        if (v.heavy_off[i] != UINT32_MAX) ++start[mo - v.heavy[i].second];
+    for (int x = 0, run = 0; x <= mo + 1; ++x) {
+        const int c = start[x];
+        start[x] = run;
+        run += c;
+    }
+    v.slot_host.assign(list.size(), make_int4(0, 0, 0, 0));
+    for (size_t i = 0; i < v.heavy.size(); ++i)
+        if (v.heavy_off[i] != UINT32_MAX)
+            v.slot_host[start[mo - v.heavy[i].second]++] =
+                make_int4(v.heavy[i].first, 1 << 16, (int)v.heavy_off[i], v.heavy[i].second);
+    if ((int64_t)v.slot_host.size() > v.slot_cap) {
+        cudaFree(v.slot_dev);
+        v.slot_dev = nullptr;
+        v.slot_cap = 0;
+        e = gz_malloc(&v.slot_dev, sizeof(int4) * v.slot_host.size());
+        if (e != cudaSuccess) return cuda_fail(e, "clique: heavy slots");
+        v.slot_cap = (int64_t)v.slot_host.size();
+    }
+    e = cudaMemcpyAsync(v.slot_dev, v.slot_host.data(), sizeof(int4) * v.slot_host.size(),
+                        cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "clique: heavy slots");
     return GZ_OK;
 }
 
@@ -718,42 +1087,64 @@ gz_status launch_k(const GzView& v, int64_t n, int64_t lo, int64_t hi, cudaStrea
     if (st != GZ_OK) return st;
     st = build_heavy_rows(mv, mo, sms, s);
     if (st != GZ_OK) return st;
-    // heavy roots of [lo, hi) with cached rows, heaviest first, each split into parts
-    std::vector<int> hi_idx;
-    auto it = std::lower_bound(mv.heavy.begin(), mv.heavy.end(), std::make_pair((int32_t)lo, INT32_MIN));
-    for (; it != mv.heavy.end() && it->first < hi; ++it) {
-        const size_t i = (size_t)(it - mv.heavy.begin());
-        if (mv.heavy_rows_ok && mv.heavy_off[i] != UINT32_MAX) hi_idx.push_back((int)i);
-    }
-    std::stable_sort(hi_idx.begin(), hi_idx.end(), [&](int a, int b) {
-        return mv.heavy[a].second > mv.heavy[b].second;
-    });
+    // heavy roots of [lo, hi) with cached rows, heaviest first: for K <= 5 the
+    // view's slot list (on the device already when all roots are counted), for
+    // K >= 6 each root split into parts_for(K, d) slots
     std::vector<int4> ent;
-    for (int i : hi_idx) {
-        const int parts = parts_for(K, mv.heavy[i].second);
-        for (int p = 0; p < parts; ++p)
-            ent.push_back(make_int4(mv.heavy[i].first, p | (parts << 16), (int)mv.heavy_off[i], 0));
+    const int4* d_slots = nullptr;
+    int nslots = 0;
+    if (K <= 5 && mv.heavy_rows_ok && lo <= 0 && hi >= n) {
+        d_slots = mv.slot_dev;
+        nslots = (int)mv.slot_host.size();
+    } else if (K <= 5) {
+        if (mv.heavy_rows_ok)
+            for (const int4& x : mv.slot_host)
+                if (x.x >= lo && x.x < hi) ent.push_back(x);
+    } else if (mv.heavy_rows_ok) {
+        for (const int4& x : mv.slot_host) {
+            if (x.x < lo || x.x >= hi) continue;
+            const int parts = parts_for(K, x.w);
+            for (int p = 0; p < parts; ++p) ent.push_back(make_int4(x.x, p | (parts << 16), x.z, x.w));
+        }
     }
     // without cached rows no root is split (the chunk slots then take them all)
     const int heavy_d = mv.heavy_rows_ok ? kHeavyD : mo + 1;
-    const size_t smem = ((size_t)mo * (((mo + 31) / 32) | 1) + 2 * (size_t)mo + 1) * 4;
+    const size_t smem = ((size_t)mo * (K <= 5 ? row_stride(mo) : (((mo + 31) / 32) | 1)) + 2 * (size_t)mo + 1) * 4;
     int4* d_ent = nullptr;
     cudaError_t e = cudaSuccess;
     if (!ent.empty()) {
         e = gz_malloc_async(&d_ent, sizeof(int4) * ent.size(), s);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(d_ent, ent.data(), sizeof(int4) * ent.size(), cudaMemcpyHostToDevice, s);
+        d_slots = d_ent;
+        nslots = (int)ent.size();
     }
     if (e == cudaSuccess) {
-        cudaFuncSetAttribute(k_clique_big<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clique_big<K>, kBigThreads, smem);
-        int bb = sms * (per_sm > 0 ? per_sm : 1);
-        const int64_t slots = (int64_t)ent.size() + (nroots + kBigPop - 1) / kBigPop;
-        if (slots < bb) bb = (int)std::max<int64_t>(1, slots);
-        k_clique_big<K><<<bb, kBigThreads, smem, s>>>(v.dag_rp, v.dag_col, lo, hi, mo, heavy_d, d_ent,
-                                                       (int)ent.size(), mv.heavy_rows, d_work + 1, d_count);
-        GZ_COUNT_LAUNCH();
-        e = cudaGetLastError();
+        const int64_t slots = (int64_t)nslots + (nroots + kBigPop - 1) / kBigPop;
+        if constexpr (K <= 5) {
+            e = cudaFuncSetAttribute(k_clique_warp<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clique_warp<K>, kWarpCta, smem);
+            int bb = sms * (per_sm > 0 ? per_sm : 1);
+            if (slots < bb) bb = (int)std::max<int64_t>(1, slots);
+            if (e == cudaSuccess) {
+                k_clique_warp<K><<<bb, kWarpCta, smem, s>>>(v.dag_rp, v.dag_col, lo, hi, mo, heavy_d, d_slots,
+                                                             nslots, mv.heavy_rows, d_work + 1, d_count);
+                GZ_COUNT_LAUNCH();
+            }
+        } else {
+            e = cudaFuncSetAttribute(k_clique_big<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clique_big<K>, kBigThreads, smem);
+            int bb = sms * (per_sm > 0 ? per_sm : 1);
+            if (slots < bb) bb = (int)std::max<int64_t>(1, slots);
+            if (e == cudaSuccess) {
+                k_clique_big<K><<<bb, kBigThreads, smem, s>>>(v.dag_rp, v.dag_col, lo, hi, mo, heavy_d, d_slots,
+                                                               nslots, mv.heavy_rows, d_work + 1, d_count);
+                GZ_COUNT_LAUNCH();
+            }
+        }
+        if (e == cudaSuccess) e = cudaGetLastError();
     }
     if (d_ent) cudaFreeAsync(d_ent, s);
     if (e != cudaSuccess) return cuda_fail(e, "clique launch");

@@ -95,6 +95,11 @@ struct GzView {
     std::vector<uint32_t> heavy_off;
     bool heavy_rows_built = false;  // the build has run for this out-list view
     bool heavy_rows_ok = false;     // ... and left rows in heavy_rows
+    // the cached roots as clique-kernel slots (root, 1 << 16, row offset,
+    // out-degree), heaviest first: host copy and device copy (kept across rebuilds)
+    std::vector<int4> slot_host;
+    int4* slot_dev = nullptr;
+    int64_t slot_cap = 0;
 };
 
 struct gz_graph {
