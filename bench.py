@@ -11,7 +11,10 @@ loops consume (computed by the CPU oracle and stored in tests/golden).
 
 Other workloads (--config): triangle (ER 4096, plain method), patterns (R-MAT
 22, five patterns), batched (64 queries over 16 graphs, one launch vs one per
-launch), served (Poisson request stream on R-MAT 24 vs FIFO one-per-launch).
+launch), served (Poisson request stream on a device-resident R-MAT graph, scale
+24 by default, against FIFO one query per launch), motifs, schedules, planner.
+The default run also prints short triangle / patterns / batched records
+(--no-subconfigs skips them).
 
 --impl reference times the CPU oracle on a bounded sample of the same workload.
 Under torchrun each rank runs a replica of the workload on its own GPU (weak
@@ -141,12 +144,13 @@ def measured_peaks():
 
 
 def kernel_source_hash():
-    """Hash of the source of k_clique_big and the device helpers it runs (the
+    """Hash of the source of k_clique_warp and the device helpers it runs (the
     kernel the roofline figures are for); the whole file if the markers move."""
     src = open(os.path.join(ROOT, "paper_1911_12877_gb300", "csrc", "gz_clique.cu")).read()
     parts = []
-    for a, b in (("// Sum over the cliques that extend", "// Rows of every heavy root, built once"),
-                 ("// Roots with 32 < |O| <= max_out: one CTA per root", "// Roots whose out-list is too long")):
+    for a, b in (("// Row stride (32-bit words) of the bitset rows", "// Index of x in sorted O[0, n)"),
+                 ("// K = 4 and K = 5 on roots with 32 < |O| <= max_out: k_clique_warp.",
+                  "// Roots whose out-list is too long for shared-memory rows")):
         i, j = src.find(a), src.find(b)
         if i < 0 or j < i:
             parts = [src]
@@ -158,9 +162,12 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+PROFILE_K5 = "k_clique_warp_k5_rmat20.json"
+
+
 def profiled(name: str):
-    """Figures of a committed ncu summary (DRAM bytes per launch, issue-slot use),
-    if it was taken on the current kernel source; else None."""
+    """Figures of a committed ncu summary (DRAM bytes per launch, pipe use), if
+    it was taken on the current kernel source; else None."""
     path = os.path.join(PROFILES, name)
     if not os.path.exists(path):
         return None
@@ -171,6 +178,41 @@ def profiled(name: str):
     if d.get("kernel_source_sha") != kernel_source_hash():
         return None
     return d
+
+
+#: popcount results per clock per SM: the instruction runs on the SM's XU pipe,
+#: a quarter of the 64-lane integer ALU rate (NVIDIA's arithmetic-instruction
+#: throughput table for compute capabilities 7.x-10.x); the committed ncu
+#: summary of the clique kernel states the XU pipe's own utilisation beside it
+XU_POPC_PER_CLK_SM = 16
+
+
+def clique_roofline(words, kernel_s, e_elems, clocks, sms, prof):
+    """Roofline of the K5 clique count. Its work is bitset word operations (one
+    32-bit word of a candidate set ANDed and popcounted or walked), counted
+    exactly by the oracle's bitset work measure; every word of the last loop
+    takes one popcount, so the bound is the SMs' popcount rate at the sampled
+    SM clock."""
+    mhz = clocks.get("sm_mhz") or 2070.0
+    peak = XU_POPC_PER_CLK_SM * sms * mhz * 1e6 / 1e9
+    achieved = words / kernel_s / 1e9
+    hbm, hbm_kind = measured_peaks()
+    traffic = prof.get("dram_bytes_per_launch") if prof else None
+    return {"bound": "alu", "kernel": "k_clique_small<5> + k_clique_warp<5> (K5 count)",
+            "achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "Gword-op/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic,
+            "peak_kind": f"derived: {XU_POPC_PER_CLK_SM} popcounts/clk/SM x {sms} SMs x {mhz:.0f} MHz "
+                         "(median SM clock sampled during the timed region)",
+            "kernel_ms": round(kernel_s * 1e3, 3), "algorithmic_words": words,
+            "e_rate_over_hbm_peak": round(4.0 * e_elems / kernel_s / 1e9 / hbm, 3),
+            "hbm_peak_gbs": hbm, "hbm_peak_kind": hbm_kind,
+            "dram_frac": (round(traffic / kernel_s / 1e9 / hbm, 6) if traffic else None),
+            "xu_pipe_pct_ncu": prof.get("xu_pipe_pct") if prof else None,
+            "issue_active_pct_ncu": prof.get("issue_active_pct") if prof else None,
+            "note": "achieved = bitset word operations of the K5 loops (oracle, exact) / K5 count time "
+                    "(CUDA events); e_rate_over_hbm_peak = 4 x E / t over the HBM copy peak, E = list "
+                    "elements the paper's bounded linear scans would consume: the bitset kernel reads each "
+                    "root's rows from shared memory, so that ratio exceeds 1 and is not a roofline fraction"}
 
 
 def flush_l2(buf):
@@ -195,9 +237,10 @@ def clique_workload():
     return g, gold
 
 
-def cpu_baseline_clique(g, gold, target_s: float = 12.0, max_s: float = 40.0):
+def cpu_baseline_clique(g, gold, target_s: float = 12.0, max_s: float = 40.0, nthreads: int = 0):
     """The oracle as it stands on a bounded sample: roots in 16 evenly spaced
-    ranges of width w of the reindexed graph, K4 and K5, all host threads."""
+    ranges of width w of the reindexed graph, K4 and K5, all host threads (or
+    nthreads)."""
     import oracle as O
     from synthetic.patterns import adjacency
     go, _ = O.reindex(g)
@@ -209,14 +252,15 @@ def cpu_baseline_clique(g, gold, target_s: float = 12.0, max_s: float = 40.0):
         e = 0
         for a, order in pats:
             for s in starts:
-                e += O.count_nested(a, order, go, s, min(g.n, s + w))[1]
+                e += O.count_nested(a, order, go, s, min(g.n, s + w), nthreads=nthreads)[1]
         t = time.perf_counter() - t0
         if t >= target_s or t * 2 > max_s or w >= g.n // 16:
             break
         w = max(w * 2, int(w * target_s / max(t, 1e-3) * 0.9))
-    return {"value": e / t, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+    cores = nthreads if nthreads > 0 else O.threads()
+    return {"value": e / t, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"K4+K5 on R-MAT 20 (reindexed), roots in 16 ranges of {w} ids "
-                      f"starting at i*n/16+4096; E={e} in {t:.2f} s"}, w, starts
+                      f"starting at i*n/16+4096; E={e} in {t:.2f} s on {cores} thread(s)"}, w, starts
 
 
 def run_clique(args, dist, world, rank, local):
@@ -274,23 +318,10 @@ def run_clique(args, dist, world, rank, local):
     elapsed = sum(step_ms) / 1e3
     elapsed_max, units = aggregate(dist, elapsed, e_total * args.steps)
     value = units / elapsed_max
-    peak, peak_kind = measured_peaks()
     k5_s = statistics.mean(k5_ms) / 1e3
-    achieved = 4.0 * e_k5 / k5_s / 1e9
-    prof = profiled("k_clique_big_k5_rmat20.json")
-    traffic = prof.get("dram_bytes_per_launch") if prof else None
-    roofline = {"bound": "hbm", "kernel": "k_clique_small<5> + k_clique_big<5> (K5 count)",
-                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic,
-                "peak_kind": peak_kind, "kernel_ms": round(k5_s * 1e3, 3),
-                "algorithmic_bytes": 4 * e_k5,
-                "dram_frac": (round(traffic / k5_s / 1e9 / peak, 6) if traffic else None),
-                "issue_frac": (prof.get("issue_active_pct", 0) / 100 if prof else None),
-                "note": "algorithmic bytes = 4 x E, E = list elements the paper's bounded linear "
-                        "scans consume (oracle); the bitset kernel reuses each root's rows on chip, "
-                        "so 4E/t exceeds the HBM copy peak while its DRAM traffic (ncu) is a small "
-                        "fraction of it: the kernel is bound by instruction issue (issue_frac = "
-                        "busy issue slots of k_clique_big<5>, ncu)"}
+    clocks = clk.summary()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    roofline = clique_roofline(gold["k5"]["bitset_words"], k5_s, e_k5, clocks, sms, profiled(PROFILE_K5))
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timing
     e2e = None
@@ -342,6 +373,10 @@ def run_clique(args, dist, world, rank, local):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_clique(g, gold)[0]
+        cpu["single_thread"] = cpu_baseline_clique(g, gold, target_s=8.0, max_s=25.0, nthreads=1)[0]
+    subs = None
+    if rank == 0 and world == 1 and not args.no_subconfigs:
+        subs = sub_records(args, dist, world, rank, local)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1e3 * elapsed_max / args.steps, 3),
@@ -356,9 +391,35 @@ def run_clique(args, dist, world, rank, local):
         "step_ms": [round(x, 3) for x in step_ms],
         "plan_ms": plan_ms, "orient_ms": round(statistics.median(o_ms), 3),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clk.summary(),
+        "clocks": clocks,
     }
+    if subs is not None:
+        line["subconfigs"] = subs
     return line
+
+
+def sub_records(args, dist, world, rank, local):
+    """Short runs of the triangle (ER 4096), arbitrary-pattern (R-MAT 22 oracle
+    samples, counts re-checked) and batched (64 queries, counts checked against
+    the oracle's values) workloads, each with its own clock record."""
+    import argparse as _ap
+    out = {}
+    for name, fn, kw in (("triangle", run_triangle, {"steps": 20}),
+                         ("patterns_rmat22", run_patterns, {"steps": 3}),
+                         ("batched", run_batched, {"steps": 2})):
+        a = _ap.Namespace(**vars(args))
+        for k, v in kw.items():
+            setattr(a, k, v)
+        a.warmup = 1
+        t0 = time.perf_counter()
+        with ClockSampler(local) as clk:
+            rec = fn(a, dist, world, rank, local)
+        rec["clocks"] = clk.summary()
+        rec["wall_s"] = round(time.perf_counter() - t0, 2)
+        for k in ("n_gpus", "steps", "warmup", "scaling", "vs_baseline", "dtype", "data"):
+            rec.pop(k, None)
+        out[name] = rec
+    return out
 
 
 def run_reference(args, world, rank):
@@ -549,14 +610,40 @@ def run_batched(args, dist, world, rank, local):
                                stream)
     if batch != plain:
         raise SystemExit("batched counts differ from one-per-launch counts")
+    parity = batched_oracle_parity(table, batch, plans, graphs)
     mb, mp = statistics.median(ms_b), statistics.median(ms_p)
     return _line("queries/s, batched (one gz_count_batch call)", len(table) / (mb / 1e3), "queries/s",
                  args, world, mb,
                  {"workload": f"{len(table)} queries over {len(graphs)} R-MAT graphs (scales 10..{top}, "
                               f"ef 8..32, seeds 100+i), query table seed 4", "queries": len(table)},
                  plain_queries_per_s=len(table) / (mp / 1e3), speedup_vs_plain=mp / mb,
+                 oracle_parity=parity,
                  batched=_summary(ms_b), plain=_summary(ms_p), gpu_launches_per_batch=lb // (args.steps + 1),
                  counts=[int(x) for x in batch])
+
+
+def batched_oracle_parity(table, counts, plans, graphs):
+    """Checks the batched counts against the oracle's stored values: the full
+    count where the oracle finished, else its sampled root ranges (counted here
+    through gz_count_ex). Returns "ok" or exits."""
+    import paper_1911_12877_gb300 as gz
+    gold = load_golden("batched_table.json")
+    full = sampled = 0
+    for (gi, name), c in zip(table, counts):
+        r = gold["results"].get(f"{gi}:{name}")
+        if r is None:
+            raise SystemExit(f"batched_table.json has no oracle value for graph {gi} {name}")
+        if "count" in r:
+            if c != r["count"]:
+                raise SystemExit(f"batched graph {gi} {name}: {c} != oracle {r['count']}")
+            full += 1
+        else:
+            for lo, hi, want, _ in r["samples"]:
+                got = gz.count(plans[name], graphs[gi], True, lo, hi)
+                if got != want:
+                    raise SystemExit(f"batched graph {gi} {name} roots [{lo},{hi}): {got} != oracle {want}")
+            sampled += 1
+    return {"status": "ok", "full_counts": full, "sampled_ranges": sampled}
 
 
 def run_served(args, dist, world, rank, local):
@@ -775,6 +862,8 @@ def main(argv=None):
                              "schedules", "planner"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-subconfigs", action="store_true",
+                    help="skip the short triangle / patterns / batched records of the default run")
     ap.add_argument("--scale", type=int, default=0, help="R-MAT scale override (smaller cases)")
     ap.add_argument("--patterns", default="", help="patterns config: comma-separated subset")
     ap.add_argument("--cutoff", type=float, default=8.0,

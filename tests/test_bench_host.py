@@ -47,6 +47,6 @@ def test_committed_profile_matches_kernel_source():
     """The committed ncu summary of the dominant kernel was taken on the current
     source of that kernel, so the bench can report its DRAM traffic (a changed
     kernel must be profiled again, and its traffic reads null until then)."""
-    d = bench.profiled("k_clique_big_k5_rmat20.json")
-    assert d is not None, "k_clique_big changed since its ncu capture"
+    d = bench.profiled(bench.PROFILE_K5)
+    assert d is not None, "k_clique_warp changed since its ncu capture"
     assert d["dram_bytes_per_launch"] == d["dram_bytes_read"] + d["dram_bytes_write"]
