@@ -296,7 +296,8 @@ gz_status launch_mixed(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream
         const int64_t hi = (q.root_hi < 0 || q.root_hi > q.g->n) ? q.g->n : q.root_hi;
         cudaStream_t t = fork((int)c + 1);
         used.push_back(t);
-        st = clique_launch(q.plan->k, *q.view, q.g->n, lo, hi, t, d_counts + cliq[c], d_work + 3 * cliq[c]);
+        st = clique_launch(q.plan->k, *q.view, q.g->n, lo, hi, t, d_counts + cliq[c],
+                           d_work + kCliqueWork * cliq[c]);
     }
     // join: s waits for every stream used
     for (cudaStream_t t : used) {
@@ -329,8 +330,9 @@ gz_status run_queries(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream_
         if (st != GZ_OK) return st;
         return count_one_in_region(q, cfg, s, a.ptr, a.bytes - meta, true, out_counts);
     }
-    // arena: counts [nq], status, clique work counters [3 nq] | launch metadata | scratch
-    const uint64_t head = ((sizeof(unsigned long long) * (4 * (uint64_t)nq + 1)) + 255) & ~255ull;
+    // arena: counts [nq], status, clique work counters [kCliqueWork nq] | launch metadata | scratch
+    const size_t hwords = (size_t)nq + 1 + kCliqueWork * (size_t)nq;
+    const uint64_t head = ((sizeof(unsigned long long) * hwords) + 255) & ~255ull;
     const uint64_t meta = (mixed_meta_bytes(qs, nq) + 255) & ~255ull;
     const uint64_t need = head + meta + mixed_scratch_bytes(qs, nq, cfg);
     gz_status st = arena_reserve(a, need);
@@ -338,7 +340,7 @@ gz_status run_queries(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream_
     unsigned long long* d = reinterpret_cast<unsigned long long*>(a.ptr);
     char* mp = reinterpret_cast<char*>(a.ptr) + head;
     int* d_status = reinterpret_cast<int*>(d + nq);
-    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned long long) * (4 * (size_t)nq + 1), s);
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned long long) * hwords, s);
     if (e != cudaSuccess) return cuda_fail(e, "memset counts");
     st = launch_mixed(qs, nq, cfg, s, d, d_status, d + nq + 1, mp + meta, a.bytes - head - meta, mp, meta, true);
     std::vector<unsigned long long> h(nq + 1);

@@ -536,19 +536,13 @@ __device__ __forceinline__ uint32_t k5_pair(const uint4* __restrict__ rows4, int
     return cnt;
 }
 
-template <int K>
-__device__ __forceinline__ uint32_t warp_pair(const uint4* rows4, int Ws4, int wm, int a, int b) {
-    if constexpr (K == 4) {
-        (void)wm;
-        return k4_pair(rows4, Ws4, a, b);
-    } else {
-        switch (wm) {
-            case 8: return k5_pair<8>(rows4, Ws4, a, b);
-            case 16: return k5_pair<16>(rows4, Ws4, a, b);
-            case 24: return k5_pair<24>(rows4, Ws4, a, b);
-            default: return k5_pair<32>(rows4, Ws4, a, b);
-        }
-    }
+// nw: words of the widest pair among the warp's active lanes (the same for all
+// lanes, so the warp runs one instantiation of k5_pair).
+__device__ __forceinline__ uint32_t k5_pair_any(const uint4* rows4, int Ws4, int a, int b, int nw) {
+    if (nw <= 8) return k5_pair<8>(rows4, Ws4, a, b);
+    if (nw <= 16) return k5_pair<16>(rows4, Ws4, a, b);
+    if (nw <= 24) return k5_pair<24>(rows4, Ws4, a, b);
+    return k5_pair<32>(rows4, Ws4, a, b);
 }
 
 template <int K>
@@ -612,7 +606,6 @@ __global__ void __launch_bounds__(kWarpCta, 2) k_clique_warp(const int64_t* __re
             __syncthreads();
             const uint4* rows4 = reinterpret_cast<const uint4*>(rows);
             const int Ws4 = Ws >> 2;
-            const int wm = ((((d + 31) >> 5) + 7) >> 3) << 3;
             for (;;) {
                 int m = 0;
                 if (lane == 0) m = atomicAdd(&s_next, 1);
@@ -647,10 +640,9 @@ __global__ void __launch_bounds__(kWarpCta, 2) k_clique_warp(const int64_t* __re
                     }
                     const uint32_t ww = __shfl_sync(kFull, word, wlo);
                     const int before = __shfl_sync(kFull, incl, wlo) - __popc(ww);
-                    if (j < total) {
-                        const int b = (wlo << 5) + select_bit(ww, j - before);
-                        acc += warp_pair<K>(rows4, Ws4, wm, a, b);
-                    }
+                    const int b = j < total ? (wlo << 5) + select_bit(ww, j - before) : 0;
+                    const int nw = __reduce_max_sync(kFull, (unsigned)((b + 31) >> 5));
+                    if (j < total) acc += k5_pair_any(rows4, Ws4, a, b, nw);
                 }
             }
             __syncthreads();
@@ -1181,7 +1173,7 @@ gz_status clique_prepare(const GzView& v, int64_t n, cudaStream_t s) {
 
 // Adds the cliques of the roots in [lo, hi) whose out-list holds at most
 // kCliqueLongOut vertices to *d_count; longer roots are left to the caller.
-// d_work holds three zeroed counters.
+// d_work holds kCliqueWork zeroed counters.
 gz_status clique_launch(int k, const GzView& v, int64_t n, int64_t lo, int64_t hi, cudaStream_t s,
                         unsigned long long* d_count, unsigned long long* d_work) {
     if (hi <= lo) return GZ_OK;

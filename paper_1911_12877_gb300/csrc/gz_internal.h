@@ -209,12 +209,13 @@ gz_status count_one_in_region(const Query& Q, const LaunchCfg& cfg, cudaStream_t
 
 // clique side (gz_clique.cu): oriented k-cliques as bitsets over the root's out-list
 constexpr int kCliqueMaxOut = 1024;   // largest out-list whose rows fit in shared memory
+constexpr int kCliqueWork = 3;        // zeroed work counters a clique query needs
 constexpr int kCliqueLongOut = 8192;  // largest out-list of the clique kernels (rows in global)
 bool clique_eligible(const GzProg& p, const gz_plan& plan, const GzView& v);
 // Enqueues nq queries on stream s: oriented cliques on the bitset kernels (their
 // roots with out-lists longer than kCliqueLongOut on the general kernel), the rest
 // in one persistent general launch. Query i adds its count to d_counts[i];
-// d_work holds 3 zeroed counters per query; scratch as for count_launch; meta
+// d_work holds kCliqueWork zeroed counters per query; scratch as for count_launch; meta
 // holds mixed_meta_bytes(qs, nq) bytes for the general launch. With overlap, a
 // mix of queries forks onto a per-device stream pool and joins s again (the
 // server passes false: its slots already overlap on their own streams).

@@ -110,8 +110,8 @@ gz_status launch_batch(gz_server* s, Slot& sl) {
     }
     const uint64_t meta = (mixed_meta_bytes(qs.data(), nq) + 255) & ~255ull;
     const uint64_t need = meta + mixed_scratch_bytes(qs.data(), nq, kCfg) + 256;
-    // counts [nq], status, clique work counters [3 nq]
-    const size_t words = (size_t)nq + 1 + 3 * (size_t)nq;
+    // counts [nq], status, clique work counters [kCliqueWork nq]
+    const size_t words = (size_t)nq + 1 + kCliqueWork * (size_t)nq;
     void* scratch = nullptr;
     unsigned long long* d = nullptr;
     cudaError_t e = gz_malloc_async(&scratch, need, sl.stream);

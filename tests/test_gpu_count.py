@@ -338,6 +338,24 @@ def test_cliques_with_out_lists_beyond_the_bitset_limit():
     assert gz.count(gz.Plan("k4"), G, orientation=True) == oracle_count("k4", g)
 
 
+def test_cliques_on_multipartite_long_out_lists():
+    """Complete 16-partite graph with parts of 75: every vertex has degree 1125,
+    so oriented out-lists run past 1024 (the long-root launch of the K4/K5
+    kernels and their wide pairs, b >= 1024). A k-clique takes one vertex from
+    each of k parts: C(16, k) * 75^k of them (closed form)."""
+    import math
+    parts, r = 16, 75
+    n = parts * r
+    idx = np.arange(n)
+    src, dst = np.meshgrid(idx, idx, indexing="ij")
+    keep = (src < dst) & (src // r != dst // r)
+    e = np.stack([src[keep], dst[keep]], 1).astype(np.int32)
+    G = gz.Graph.from_csr(S.from_edges(n, e, "K16x75")).orient()
+    assert G.info()["max_out_degree_oriented"] > 1024
+    for k in (4, 5):
+        assert gz.count(gz.Plan(f"k{k}"), G, orientation=True) == math.comb(parts, k) * r ** k, k
+
+
 @pytest.mark.parametrize("name", ["diamond", "paw", "c4", "house", "chordal5", "hourglass"])
 def test_split_units_book_graph(name):
     """Units whose loop-2 candidate list reaches the split threshold (512) are
