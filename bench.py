@@ -646,54 +646,118 @@ def batched_oracle_parity(table, counts, plans, graphs):
     return {"status": "ok", "full_counts": full, "sampled_ranges": sampled}
 
 
+def _alone_time(gz, p, G, n, cap_s, piece_s=0.5):
+    """Service time of one request alone, bounded: the roots are counted in
+    consecutive ranges sized to take about piece_s each (from the previous
+    range's rate, within 4x), hub end first, until all are counted or cap_s has
+    passed. Returns (seconds, roots counted, count over them)."""
+    import time as _t
+    lo, width, total, spent = 0, 1, 0, 0.0
+    while lo < n and spent < cap_s:
+        hi = min(n, lo + width)
+        t0 = _t.perf_counter()
+        total += gz.count(p, G, True, lo, hi)
+        dt = _t.perf_counter() - t0
+        spent += dt
+        lo = hi
+        width = int(min(4 * width, max(width / 4, width * piece_s / max(dt, 1e-4)))) or 1
+    return spent, lo, total
+
+
 def run_served(args, dist, world, rank, local):
     """Poisson request stream over a device-resident R-MAT graph and its oriented
-    copy: continuous batching vs FIFO one query per launch, p50/p99 latency.
+    copy: continuous batching (fast requests batched on free streams; a slow one
+    at a time on a share of the device, so fast ones run beside it) against
+    FIFO, one whole-graph query per launch in arrival order. The slow threshold
+    is twice the median service time alone of the stream's patterns unless
+    --heavy-ms is given.
 
-    Default scale 14 (ef 16, seed 14): one request costs about a millisecond
-    (triangle, cliques, c4) to tens of milliseconds (chordal 5-cycle), so the
-    rate sweep runs from a lightly loaded to an overloaded server. On R-MAT 16
-    the mix already saturates the GPU at 6.5 requests/s (measured), and on
-    R-MAT 22 one full c4 count takes 132 s, so the larger graphs cannot carry
-    a request stream at these rates."""
+    Default graph: R-MAT scale 24 (ef 16, seed 24). Each pattern of the request
+    mix is first measured alone, bounded by --alone-cap seconds (roots counted in
+    growing ranges, hub end first): a pattern whose count finishes within the cap
+    joins the stream; the others (c4, diamond and the chordal 5-cycle need
+    minutes per count on this graph) are reported with the roots they covered
+    and the time, a lower bound of their service time. Every served and FIFO
+    result must equal its count alone, and the oracle's sampled root ranges of
+    the graph (tests/golden/served_rmat24.json) are counted and compared."""
     import numpy as np
     import torch
     import paper_1911_12877_gb300 as gz
     import synthetic as S
     from synthetic.patterns import SERVED_PATTERNS
     torch.cuda.set_device(local)
-    scale = args.scale or 14
+    scale = args.scale or 24
     g = S.rmat(scale, 16, scale)
     G = gz.Graph.from_csr(g).orient()
-    plans = [gz.Plan(n) for n in SERVED_PATTERNS]
-    alone = [gz.count(p, G, True) for p in plans]
-    nreq = args.requests
+    names = args.patterns.split(",") if args.patterns else SERVED_PATTERNS
+    alone, stream = {}, []
+    for name in names:
+        p = gz.Plan(name)
+        secs, roots, cnt = _alone_time(gz, p, G, g.n, args.alone_cap)
+        rec = {"roots_counted": roots, "of": g.n, "seconds": round(secs, 3)}
+        if roots == g.n:
+            import time as _t
+            t0 = _t.perf_counter()
+            c = gz.count(p, G, True)
+            rec.update(count=c, whole_count_s=round(_t.perf_counter() - t0, 3))
+            if c != cnt:
+                raise SystemExit(f"{name}: whole count {c} != sum of its root ranges {cnt}")
+            stream.append(name)
+        else:
+            rec["note"] = "cap reached: the full count takes longer than these seconds"
+        alone[name] = rec
+    parity = None
+    if scale == 24 and os.path.exists(os.path.join(GOLDEN, "served_rmat24.json")):
+        gold = load_golden("served_rmat24.json")
+        if gold["nnz"] != g.nnz:
+            raise SystemExit("served_rmat24.json does not match the generated graph")
+        checked = 0
+        for name, rec in gold["patterns"].items():
+            p = gz.Plan(name)
+            for lo, hi, want, _ in rec["samples"]:
+                got = gz.count(p, G, True, lo, hi)
+                if got != want:
+                    raise SystemExit(f"served graph {name} roots [{lo},{hi}): {got} != oracle {want}")
+                checked += 1
+        parity = {"status": "ok", "sampled_ranges": checked}
+    if not stream:
+        raise SystemExit("no pattern of the mix finishes within --alone-cap")
+    plans = [gz.Plan(n) for n in stream]
+    counts_alone = [alone[n]["count"] for n in stream]
+    mean_s = float(np.mean([alone[n]["whole_count_s"] for n in stream]))
+    heavy_ms = args.heavy_ms or max(1.0, 2e3 * float(np.median([alone[n]["whole_count_s"] for n in stream])))
+    nreq = args.requests or (300 if mean_s < 0.05 else max(6, int(60.0 / max(mean_s, 1e-3))))
+    rates = args.rates or ("12.5,25,50,100,200" if mean_s < 0.05 else "12.5,200")
     out = {}
-    for lam in [float(x) for x in args.rates.split(",")]:
+    for lam in [float(x) for x in rates.split(",")]:
         rng = np.random.default_rng(5)
         arr = np.cumsum(rng.exponential(1e9 / lam, nreq)).astype(np.int64)
         pidx = rng.integers(0, len(plans), nreq).astype(np.int32)
         gidx = np.zeros(nreq, np.int32)
-        rec = {}
+        rec = {"offered_rps": lam, "offered_load": round(lam * mean_s, 3)}
         for mode in ("served", "fifo"):
-            srv = gz.Server(max_inflight=args.inflight, max_batch=args.max_batch, heavy_ms=args.heavy_ms)
+            srv = gz.Server(max_inflight=args.inflight, max_batch=args.max_batch, heavy_ms=heavy_ms,
+                            slow_share=args.slow_share)
             counts, lat, st = srv.replay(plans, [G], [1] * nreq, arr, pidx, gidx, fifo=(mode == "fifo"))
             srv.close()
-            if [int(c) for c in counts] != [alone[i] for i in pidx]:
+            if [int(c) for c in counts] != [counts_alone[i] for i in pidx]:
                 raise SystemExit(f"{mode} counts differ from counts alone")
             ms = np.sort(lat) / 1e6
             rec[mode] = {"p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
-                         "achieved_rps": st["achieved_rps"], "max_queue": int(st["max_queue"]),
-                         "launches": int(st["launches"]), "wall_s": st["wall_s"]}
+                         "mean_ms": float(ms.mean()), "achieved_rps": st["achieved_rps"],
+                         "max_queue": int(st["max_queue"]), "launches": int(st["launches"]),
+                         "wall_s": st["wall_s"]}
         out[str(lam)] = rec
-    lam0 = str(float(args.rates.split(",")[-1]))
+    lam0 = str(float(rates.split(",")[-1]))
     s = out[lam0]["served"]
     return _line("p99 latency, served (continuous batching)", s["p99_ms"], "ms", args, world,
                  1e3 * s["wall_s"] / nreq,
-                 {"workload": f"Poisson stream of {nreq} requests over {SERVED_PATTERNS}, R-MAT scale "
-                              f"{scale} ef 16 seed {scale} (+ oriented copy) resident",
-                  "rates_per_s": args.rates},
-                 hib=False, rates=out, counts_alone=dict(zip(SERVED_PATTERNS, alone)))
+                 {"workload": f"Poisson stream of {nreq} requests per rate over {stream}, R-MAT scale "
+                              f"{scale} ef 16 seed {scale} (+ oriented copy) resident; mix {names}",
+                  "rates_per_s": rates},
+                 hib=False, rates=out, service_alone=alone, stream_patterns=stream, heavy_ms=heavy_ms,
+                 slow_share=args.slow_share or 0.75,
+                 counts_alone=dict(zip(stream, counts_alone)), oracle_parity=parity)
 
 
 def run_motifs(args, dist, world, rank, local):
@@ -870,12 +934,20 @@ def main(argv=None):
                     help="schedules config: drop a schedule past this multiple of the best time")
     ap.add_argument("--full", default="", help="patterns config: patterns whose full count is timed "
                     "(default none at scale 22, all below)")
-    ap.add_argument("--requests", type=int, default=300, help="served config: requests per rate")
-    ap.add_argument("--rates", default="12.5,25,50,100,200", help="served config: Poisson rates")
+    ap.add_argument("--requests", type=int, default=0,
+                    help="served config: requests per rate (0: 300 for millisecond requests, else about "
+                         "60 s of service)")
+    ap.add_argument("--rates", default="", help="served config: Poisson rates (default 12.5..200, or "
+                                                "12.5,200 when requests take seconds)")
+    ap.add_argument("--alone-cap", type=float, default=20.0,
+                    help="served config: seconds a pattern may take alone before it is left out of the stream")
     ap.add_argument("--inflight", type=int, default=2, help="served config: concurrent launches")
     ap.add_argument("--max-batch", type=int, default=8, help="served config: requests per launch")
     ap.add_argument("--heavy-ms", type=float, default=0.0,
-                    help="served config: slow-request threshold in ms (0: library default, <0: off)")
+                    help="served config: slow-request threshold in ms (0: twice the median service time "
+                         "alone, <0: off)")
+    ap.add_argument("--slow-share", type=float, default=0.0,
+                    help="served config: share of the device a slow request takes (0: library default 0.75)")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "gz":
         args.warmup = 3

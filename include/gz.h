@@ -319,20 +319,24 @@ gz_status gz_count_motifs(const gz_graph* g, int k, int use_orientation, void* s
 /* --------------------------------------------------------------- serving */
 
 typedef struct {
-    int max_inflight_launches; /* concurrent batched launches (streams), >= 1 */
-    int max_batch;             /* queries per launch */
+    int max_inflight_launches; /* concurrent launches (streams), >= 1 */
+    int max_batch;             /* fast queries per launch */
     uint64_t scratch_budget;   /* device bytes for in-flight scratch, 0 = 4 GiB */
     double heavy_ms;           /* slow-request threshold (ms), 0 = 20, < 0 = none */
+    double slow_share;         /* share of the device a slow request's grids take, 0 = 0.75 */
 } gz_server_opts;
 
 /*
- * Continuous-batching request loop over device-resident graphs. Requests are
- * admitted as launch slots and scratch memory free up, batched with whatever
- * else is waiting, and run on separate streams so their work overlaps. The loop
- * keeps a moving average of each (plan, graph)'s service time when it runs
- * alone; a request above heavy_ms (or not yet measured) is launched by itself,
- * with at most one such launch in flight, and faster requests are batched
- * around it.
+ * Continuous-batching request loop over device-resident graphs. The loop keeps
+ * a moving average of each (plan, graph)'s service time when it runs alone.
+ * Fast requests (at most heavy_ms) are admitted as launch slots and scratch
+ * memory free up, batched with whatever else is waiting, and run on separate
+ * streams so their work overlaps. A slow request (above heavy_ms, or not yet
+ * measured) runs alone in its launch, one at a time. When fast requests are
+ * waiting or running and no other slow request waits, its grids take
+ * slow_share of the resident CTAs: its kernels are persistent, so the rest of
+ * the device stays free for the fast batches while it runs; otherwise it takes
+ * the whole device.
  */
 gz_status gz_server_create(const gz_server_opts* opts, gz_server** out);
 
@@ -352,8 +356,8 @@ gz_status gz_server_wait(gz_server* s, int64_t ticket, int64_t timeout_ms, uint6
  * Replays a request trace in real time: request i (plan_idx[i] into plans,
  * graph_idx[i] into graphs) is submitted at arrival_ns[i] after the call
  * starts. Fills counts[i] and latency_ns[i] (arrival to completion).
- * fifo = 1 runs the plain baseline instead: one query per launch, in arrival
- * order, one at a time. stats_out (optional, 4 values): achieved requests/s,
+ * fifo = 1 runs the plain baseline instead: one whole-graph query per launch, in
+ * arrival order, one at a time. stats_out (optional, 4 values): achieved requests/s,
  * max queue depth, launches, wall seconds.
  */
 gz_status gz_server_replay(gz_server* s, const gz_plan* const* plans,

@@ -54,7 +54,8 @@ class CountOpts(ctypes.Structure):
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("max_inflight_launches", ctypes.c_int), ("max_batch", ctypes.c_int),
-                ("scratch_budget", ctypes.c_uint64), ("heavy_ms", ctypes.c_double)]
+                ("scratch_budget", ctypes.c_uint64), ("heavy_ms", ctypes.c_double),
+                ("slow_share", ctypes.c_double)]
 
 
 _lib = None
@@ -406,8 +407,8 @@ class Server:
     """Continuous-batching request loop (gz_server)."""
 
     def __init__(self, max_inflight: int = 4, max_batch: int = 64, scratch_budget: int = 0,
-                 heavy_ms: float = 0.0):
-        o = ServerOpts(max_inflight, max_batch, scratch_budget, heavy_ms)
+                 heavy_ms: float = 0.0, slow_share: float = 0.0):
+        o = ServerOpts(max_inflight, max_batch, scratch_budget, heavy_ms, slow_share)
         h = _P()
         _check(lib().gz_server_create(ctypes.byref(o), ctypes.byref(h)), "gz_server_create")
         self.handle = h

@@ -296,7 +296,7 @@ gz_status launch_mixed(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream
         const int64_t hi = (q.root_hi < 0 || q.root_hi > q.g->n) ? q.g->n : q.root_hi;
         cudaStream_t t = fork((int)c + 1);
         used.push_back(t);
-        st = clique_launch(q.plan->k, *q.view, q.g->n, lo, hi, t, d_counts + cliq[c],
+        st = clique_launch(q.plan->k, *q.view, q.g->n, lo, hi, cfg.grid_frac, t, d_counts + cliq[c],
                            d_work + kCliqueWork * cliq[c]);
     }
     // join: s waits for every stream used

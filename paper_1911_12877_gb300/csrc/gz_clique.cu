@@ -1000,7 +1000,7 @@ gz_status build_heavy_rows(GzView& v, int mo, int sms, cudaStream_t s) {
 // roots longer than kCliqueLongOut, are left to the caller's general kernel,
 // see clique_long_cutoff), then their edges walked by k_clique_long.
 template <int K>
-gz_status launch_long(GzView& v, int64_t lo, int64_t hi, cudaStream_t s,
+gz_status launch_long(GzView& v, int64_t lo, int64_t hi, double frac, cudaStream_t s,
                       unsigned long long* d_count, unsigned long long* d_work) {
     std::vector<std::pair<int32_t, int32_t>> hr;
     auto it = std::lower_bound(v.heavy.begin(), v.heavy.end(), std::make_pair((int32_t)lo, INT32_MIN));
@@ -1041,10 +1041,10 @@ gz_status launch_long(GzView& v, int64_t lo, int64_t hi, cudaStream_t s,
         const size_t smem = sizeof(int32_t) * (kCliqueLongOut + 1);
         cudaFuncSetAttribute(k_clique_long_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_clique_long<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        const int rb = (int)std::min<size_t>(build.size(), (size_t)sms * 4);
+        const int rb = (int)std::min<size_t>(build.size(), std::max<size_t>(1, (size_t)(sms * 4 * frac)));
         k_clique_long_rows<<<rb, kThreads, smem, s>>>(v.dag_rp, v.dag_col, d_l, (int)build.size(), grows);
         GZ_COUNT_LAUNCH();
-        const int lb = (int)std::min<size_t>(ent.size(), (size_t)sms * 4);
+        const int lb = (int)std::min<size_t>(ent.size(), std::max<size_t>(1, (size_t)(sms * 4 * frac)));
         k_clique_long<K><<<lb, kThreads, smem, s>>>(v.dag_rp, d_l + build.size(), (int)ent.size(), grows,
                                                      d_work, d_count);
         GZ_COUNT_LAUNCH();
@@ -1056,15 +1056,19 @@ gz_status launch_long(GzView& v, int64_t lo, int64_t hi, cudaStream_t s,
     return GZ_OK;
 }
 
+// Grids are the resident CTAs on every SM, or the fraction frac of them (the
+// request loop runs slow requests on part of the device).
+inline int grid_part(int full, double frac) { return frac < 1.0 ? std::max(1, (int)(full * frac)) : full; }
+
 template <int K>
-gz_status launch_k(const GzView& v, int64_t n, int64_t lo, int64_t hi, cudaStream_t s,
+gz_status launch_k(const GzView& v, int64_t n, int64_t lo, int64_t hi, double frac, cudaStream_t s,
                    unsigned long long* d_count, unsigned long long* d_work) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clique_small<K>, kThreads, 0);
     const int64_t nroots = hi - lo;
-    int blocks = sms * (per_sm > 0 ? per_sm : 1);
+    int blocks = grid_part(sms * (per_sm > 0 ? per_sm : 1), frac);
     const int64_t need_small = (nroots + 32 * (kThreads / 32) - 1) / (32 * (kThreads / 32));
     if (need_small < blocks) blocks = (int)std::max<int64_t>(1, need_small);
     k_clique_small<K><<<blocks, kThreads, 0, s>>>(v.dag_rp, v.dag_col, lo, hi, d_work, d_count);
@@ -1088,16 +1092,18 @@ gz_status launch_k(const GzView& v, int64_t n, int64_t lo, int64_t hi, cudaStrea
     if (K <= 5 && mv.heavy_rows_ok && lo <= 0 && hi >= n) {
         d_slots = mv.slot_dev;
         nslots = (int)mv.slot_host.size();
-    } else if (K <= 5) {
-        if (mv.heavy_rows_ok)
-            for (const int4& x : mv.slot_host)
-                if (x.x >= lo && x.x < hi) ent.push_back(x);
     } else if (mv.heavy_rows_ok) {
-        for (const int4& x : mv.slot_host) {
-            if (x.x < lo || x.x >= hi) continue;
-            const int parts = parts_for(K, x.w);
-            for (int p = 0; p < parts; ++p) ent.push_back(make_int4(x.x, p | (parts << 16), x.z, x.w));
+        // the cached roots of [lo, hi), found in the root-sorted list, then
+        // heaviest first
+        auto it = std::lower_bound(mv.heavy.begin(), mv.heavy.end(), std::make_pair((int32_t)lo, INT32_MIN));
+        for (; it != mv.heavy.end() && it->first < hi; ++it) {
+            const size_t i = (size_t)(it - mv.heavy.begin());
+            if (mv.heavy_off[i] == UINT32_MAX) continue;
+            const int d = it->second;
+            const int parts = K <= 5 ? 1 : parts_for(K, d);
+            for (int p = 0; p < parts; ++p) ent.push_back(make_int4(it->first, p | (parts << 16), (int)mv.heavy_off[i], d));
         }
+        std::stable_sort(ent.begin(), ent.end(), [](const int4& a, const int4& b) { return a.w > b.w; });
     }
     // without cached rows no root is split (the chunk slots then take them all)
     const int heavy_d = mv.heavy_rows_ok ? kHeavyD : mo + 1;
@@ -1117,7 +1123,7 @@ gz_status launch_k(const GzView& v, int64_t n, int64_t lo, int64_t hi, cudaStrea
             e = cudaFuncSetAttribute(k_clique_warp<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e == cudaSuccess)
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clique_warp<K>, kWarpCta, smem);
-            int bb = sms * (per_sm > 0 ? per_sm : 1);
+            int bb = grid_part(sms * (per_sm > 0 ? per_sm : 1), frac);
             if (slots < bb) bb = (int)std::max<int64_t>(1, slots);
             if (e == cudaSuccess) {
                 k_clique_warp<K><<<bb, kWarpCta, smem, s>>>(v.dag_rp, v.dag_col, lo, hi, mo, heavy_d, d_slots,
@@ -1128,7 +1134,7 @@ gz_status launch_k(const GzView& v, int64_t n, int64_t lo, int64_t hi, cudaStrea
             e = cudaFuncSetAttribute(k_clique_big<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e == cudaSuccess)
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clique_big<K>, kBigThreads, smem);
-            int bb = sms * (per_sm > 0 ? per_sm : 1);
+            int bb = grid_part(sms * (per_sm > 0 ? per_sm : 1), frac);
             if (slots < bb) bb = (int)std::max<int64_t>(1, slots);
             if (e == cudaSuccess) {
                 k_clique_big<K><<<bb, kBigThreads, smem, s>>>(v.dag_rp, v.dag_col, lo, hi, mo, heavy_d, d_slots,
@@ -1140,7 +1146,7 @@ gz_status launch_k(const GzView& v, int64_t n, int64_t lo, int64_t hi, cudaStrea
     }
     if (d_ent) cudaFreeAsync(d_ent, s);
     if (e != cudaSuccess) return cuda_fail(e, "clique launch");
-    if (v.max_out > kCliqueMaxOut) return launch_long<K>(mv, lo, hi, s, d_count, d_work + 2);
+    if (v.max_out > kCliqueMaxOut) return launch_long<K>(mv, lo, hi, frac, s, d_count, d_work + 2);
     return GZ_OK;
 }
 
@@ -1174,15 +1180,15 @@ gz_status clique_prepare(const GzView& v, int64_t n, cudaStream_t s) {
 // Adds the cliques of the roots in [lo, hi) whose out-list holds at most
 // kCliqueLongOut vertices to *d_count; longer roots are left to the caller.
 // d_work holds kCliqueWork zeroed counters.
-gz_status clique_launch(int k, const GzView& v, int64_t n, int64_t lo, int64_t hi, cudaStream_t s,
+gz_status clique_launch(int k, const GzView& v, int64_t n, int64_t lo, int64_t hi, double frac, cudaStream_t s,
                         unsigned long long* d_count, unsigned long long* d_work) {
     if (hi <= lo) return GZ_OK;
     switch (k) {
-        case 4: return launch_k<4>(v, n, lo, hi, s, d_count, d_work);
-        case 5: return launch_k<5>(v, n, lo, hi, s, d_count, d_work);
-        case 6: return launch_k<6>(v, n, lo, hi, s, d_count, d_work);
-        case 7: return launch_k<7>(v, n, lo, hi, s, d_count, d_work);
-        case 8: return launch_k<8>(v, n, lo, hi, s, d_count, d_work);
+        case 4: return launch_k<4>(v, n, lo, hi, frac, s, d_count, d_work);
+        case 5: return launch_k<5>(v, n, lo, hi, frac, s, d_count, d_work);
+        case 6: return launch_k<6>(v, n, lo, hi, frac, s, d_count, d_work);
+        case 7: return launch_k<7>(v, n, lo, hi, frac, s, d_count, d_work);
+        case 8: return launch_k<8>(v, n, lo, hi, frac, s, d_count, d_work);
     }
     set_error("clique kernel: k = %d unsupported", k);
     return GZ_EINVAL;

@@ -1083,7 +1083,8 @@ gz_status count_launch(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream
     cudaError_t e = cudaMemcpyAsync(d, h.data(), sizeof(KQ) * nq, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(work, 0, 32, s);
     if (e == cudaSuccess) {
-        const int blocks = warps / cfg.block_warps;
+        int blocks = warps / cfg.block_warps;
+        if (cfg.grid_frac < 1.0) blocks = std::max(1, (int)(blocks * cfg.grid_frac));
         DeferCtl df{split ? dl : nullptr, work + 2, cap, cfg.split_min};
         k_enumerate<<<blocks, cfg.block_warps * 32, cta_smem(cfg.block_warps), s>>>(
             d, nq, total, cfg.chunk > 0 ? cfg.chunk : 1, work, d_counts, d_status,

@@ -189,6 +189,7 @@ struct LaunchCfg {
     int blocks = 0;          // 0 = auto (resident CTAs on every SM)
     int64_t split_min = 512;   // loop-2 candidates from which a unit goes to the split pass
     int64_t split_chunk = 256; // loop-2 candidates per split-pass work item
+    double grid_frac = 1.0;    // < 1: grids take this share of the resident CTAs only
 };
 uint64_t scratch_words_per_warp(const GzProg& p, const gz_graph& g, const GzView& v);
 // Device bytes count_launch needs beside the scratch (descriptors, counters,
@@ -227,7 +228,7 @@ gz_status launch_mixed(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream
 uint64_t mixed_scratch_bytes(const Query* qs, int nq, const LaunchCfg& cfg);
 uint64_t mixed_meta_bytes(const Query* qs, int nq);
 gz_status clique_prepare(const GzView& v, int64_t n, cudaStream_t s);
-gz_status clique_launch(int k, const GzView& v, int64_t n, int64_t lo, int64_t hi, cudaStream_t s,
+gz_status clique_launch(int k, const GzView& v, int64_t n, int64_t lo, int64_t hi, double frac, cudaStream_t s,
                         unsigned long long* d_count, unsigned long long* d_work);
 
 }  // namespace gz

@@ -1,14 +1,23 @@
 // gz_server.cpp - continuous-batching request loop (no paper counterpart; the
 // paper motivates just-in-time queries, Sec. 1 and Sec. 7.3).
 //
-// A worker thread owns up to max_inflight_launches CUDA streams. Whenever a
-// stream is free and requests are waiting, it admits the waiting requests in
-// arrival order while their estimated scratch fits the unused part of the
-// scratch budget, launches them as one batched persistent kernel on that
-// stream (scratch from the stream-ordered allocator), and queues an async copy
-// of the counts into pinned host memory plus an event. Completed launches are
-// detected by polling their events, so later arrivals are admitted while
-// earlier launches still run and their work overlaps on the device.
+// A worker thread owns max_inflight_launches CUDA streams ("slots"). Requests
+// fall in two classes by the service time the loop has observed for their
+// (plan, graph) pair; a pair not yet seen counts as slow:
+//  - fast requests are admitted in arrival order, as many as fit a launch and
+//    the scratch budget, and run as one batched launch on a free slot;
+//  - slow requests run one at a time, each as one launch. While fast work is
+//    waiting or running and no other slow request queues behind it, a slow
+//    launch's grids take only the share slow_share of the resident CTAs. Every
+//    kernel here is persistent (its CTAs stay until its work queue is empty),
+//    so the SM capacity it leaves free is there at once for the fast batches on
+//    the other slots: a fast request does not wait for the slow one to end.
+//    Otherwise (nothing else to run, or slow requests backed up) it takes the
+//    whole device.
+// Completions are detected by polling each slot's event, so arrivals are
+// admitted while earlier launches run and their work overlaps on the device.
+// A whole-device mode (the FIFO baseline of gz_server_replay) runs every
+// request as one full launch.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -53,11 +62,11 @@ struct Slot {
     std::vector<Req*> batch;
     uint64_t scratch = 0;
     bool busy = false;
-    bool heavy = false;              // runs one slow request alone
+    bool slow = false;          // runs one slow request on part of the device
     Clock::time_point t_launch;
 };
 
-// Observed service time of a (plan, graph) pair, from launches that ran it alone.
+// Observed service time of a (plan, graph) pair.
 struct CostKey {
     const gz_plan* p;
     const gz_graph* g;
@@ -70,17 +79,17 @@ struct gz_server {
     gz_server_opts opts{};
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
-    std::deque<Req*> pending;
+    std::deque<Req*> pending;   // arrived, not yet launched
     std::map<int64_t, Req*> reqs;
     std::vector<Slot> slots;
     std::thread worker;
     bool stop = false;
+    bool whole = false;         // whole-device mode (FIFO baseline)
     int64_t next_ticket = 1;
     uint64_t inflight_scratch = 0;
     int64_t launches = 0;
     int64_t max_queue = 0;
     int device = 0;
-    std::atomic<int> fatal{0};
     std::map<CostKey, double> cost_ms;  // moving average per (plan, graph)
 };
 
@@ -98,8 +107,9 @@ uint64_t req_scratch(const Req* r) {
     return (uint64_t)resident_warps(kCfg) * scratch_words_per_warp(r->plan->prog, *r->graph, *v) * 4 + 256;
 }
 
-// Launches slot.batch on slot.stream; called with the lock released.
-gz_status launch_batch(gz_server* s, Slot& sl) {
+// Launches the slot's requests as one batch on the slot's stream and queues the
+// read-back of their counts; the lock is released.
+gz_status launch_batch(Slot& sl, double grid_frac) {
     GZ_RANGE("gz_server_launch");
     const int nq = (int)sl.batch.size();
     std::vector<Query> qs(nq);
@@ -108,8 +118,10 @@ gz_status launch_batch(gz_server* s, Slot& sl) {
         gz_status st = prepare_query(r->plan, r->graph, r->ori, 0, -1, sl.stream, qs[i]);
         if (st != GZ_OK) return st;
     }
+    LaunchCfg cfg = kCfg;
+    cfg.grid_frac = grid_frac;
     const uint64_t meta = (mixed_meta_bytes(qs.data(), nq) + 255) & ~255ull;
-    const uint64_t need = meta + mixed_scratch_bytes(qs.data(), nq, kCfg) + 256;
+    const uint64_t need = meta + mixed_scratch_bytes(qs.data(), nq, cfg) + 256;
     // counts [nq], status, clique work counters [kCliqueWork nq]
     const size_t words = (size_t)nq + 1 + kCliqueWork * (size_t)nq;
     void* scratch = nullptr;
@@ -123,7 +135,7 @@ gz_status launch_batch(gz_server* s, Slot& sl) {
     e = cudaMemsetAsync(d, 0, sizeof(unsigned long long) * words, sl.stream);
     gz_status st = e == cudaSuccess ? GZ_OK : cuda_fail(e, "server: memset");
     if (st == GZ_OK)
-        st = launch_mixed(qs.data(), nq, kCfg, sl.stream, d, reinterpret_cast<int*>(d + nq), d + nq + 1,
+        st = launch_mixed(qs.data(), nq, cfg, sl.stream, d, reinterpret_cast<int*>(d + nq), d + nq + 1,
                           reinterpret_cast<char*>(scratch) + meta, need - meta, scratch, meta, false);
     if (st == GZ_OK) {
         e = cudaMemcpyAsync(sl.h_counts, d, sizeof(unsigned long long) * (nq + 1), cudaMemcpyDeviceToHost, sl.stream);
@@ -138,9 +150,23 @@ gz_status launch_batch(gz_server* s, Slot& sl) {
     return st;
 }
 
+void finish(gz_server* s, Req* r, gz_status st, Clock::time_point now) {
+    r->status = st;
+    r->t_done = now;
+    r->done = true;
+    s->cv_done.notify_all();
+}
+
 void worker_main(gz_server* s) {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
+    const double heavy_ms = s->opts.heavy_ms > 0 ? s->opts.heavy_ms : 20.0;
+    const double share = s->opts.slow_share > 0 && s->opts.slow_share <= 1 ? s->opts.slow_share : 0.75;
+    auto slow = [&](const Req* r) {
+        if (s->whole || s->opts.heavy_ms < 0) return false;  // whole device / class-blind
+        auto it = s->cost_ms.find(CostKey{r->plan, r->graph});
+        return it == s->cost_ms.end() || it->second > heavy_ms;
+    };
     while (!s->stop) {
         bool progress = false;
         // 1. completions
@@ -149,76 +175,76 @@ void worker_main(gz_server* s) {
             cudaError_t q = cudaEventQuery(sl.done_ev);
             if (q == cudaErrorNotReady) continue;
             auto now = Clock::now();
-            const int nq = (int)sl.batch.size();
-            int bad = *reinterpret_cast<int*>(&sl.h_counts[nq]);
-            for (int i = 0; i < nq; ++i) {
-                Req* r = sl.batch[i];
-                r->count = sl.h_counts[i];
-                r->status = q != cudaSuccess ? GZ_ECUDA : (bad ? GZ_EOVERFLOW : GZ_OK);
-                r->t_done = now;
-                r->done = true;
-            }
+            const double ms = std::chrono::duration<double, std::milli>(now - sl.t_launch).count();
             if (q != cudaSuccess) cudaGetLastError();
-            if (nq == 1 && q == cudaSuccess) {
-                const double ms = std::chrono::duration<double, std::milli>(now - sl.t_launch).count();
+            const int nq = (int)sl.batch.size();
+            const int bad = *reinterpret_cast<int*>(&sl.h_counts[nq]);
+            for (int i = 0; i < nq; ++i) {
+                sl.batch[i]->count = sl.h_counts[i];
+                finish(s, sl.batch[i], q != cudaSuccess ? GZ_ECUDA : (bad ? GZ_EOVERFLOW : GZ_OK), now);
+            }
+            if (nq == 1 && q == cudaSuccess) {  // service time of the pair, alone in its launch
                 double& c = s->cost_ms[CostKey{sl.batch[0]->plan, sl.batch[0]->graph}];
                 c = c > 0 ? 0.7 * c + 0.3 * ms : ms;
             }
             s->inflight_scratch -= sl.scratch;
             sl.batch.clear();
             sl.busy = false;
-            sl.heavy = false;
+            sl.slow = false;
             progress = true;
-            s->cv_done.notify_all();
         }
-        // 2. admission into free slots. A request whose (plan, graph) has run
-        //    alone for longer than heavy_ms (or has not run yet) is "slow": it
-        //    is launched by itself and at most one slow launch is in flight, so
-        //    slow requests do not share the GPU with each other; fast requests
-        //    are batched in arrival order around them.
-        const double heavy_ms = s->opts.heavy_ms > 0 ? s->opts.heavy_ms : 20.0;
-        auto slow = [&](const Req* r) {
-            if (s->opts.heavy_ms < 0) return false;  // class-blind admission
-            auto it = s->cost_ms.find(CostKey{r->plan, r->graph});
-            return it == s->cost_ms.end() || it->second > heavy_ms;
-        };
+        // 2. admission into free slots: fast requests batched in arrival order;
+        //    a slow request alone, on part of the device, one at a time
+        const uint64_t budget = s->opts.scratch_budget;
         for (Slot& sl : s->slots) {
             if (sl.busy || s->pending.empty()) continue;
-            bool heavy_busy = false;
-            for (const Slot& o : s->slots) heavy_busy = heavy_busy || (o.busy && o.heavy);
-            const uint64_t budget = s->opts.scratch_budget;
+            bool slow_busy = false;
+            for (const Slot& o : s->slots) slow_busy = slow_busy || (o.busy && o.slow);
             uint64_t used = 0;
             for (auto it = s->pending.begin(); it != s->pending.end() && (int)sl.batch.size() < sl.cap;) {
                 Req* r = *it;
                 const bool rs = slow(r);
-                if (rs && (heavy_busy || !sl.batch.empty())) { ++it; continue; }
-                uint64_t need = std::max(used, r->scratch);  // a batch needs its largest query's scratch
-                if (!sl.batch.empty() && s->inflight_scratch + need > budget) break;
-                if (sl.batch.empty() && s->inflight_scratch + need > budget && s->inflight_scratch > 0) break;
+                if (rs && (slow_busy || !sl.batch.empty())) { ++it; continue; }
+                const uint64_t need = std::max(used, r->scratch);  // a batch needs its largest query's scratch
+                if (s->inflight_scratch + need > budget && (s->inflight_scratch > 0 || !sl.batch.empty())) break;
                 used = need;
                 sl.batch.push_back(r);
                 it = s->pending.erase(it);
-                if (rs) {  // a slow request runs alone
-                    sl.heavy = true;
+                if (rs) {
+                    sl.slow = true;
                     break;
                 }
             }
             if (sl.batch.empty()) continue;
+            // a slow launch leaves room only when fast work needs it now, and
+            // not when slow requests queue behind it (then they are the
+            // bottleneck and take the whole device)
+            double frac = 1.0;
+            if (sl.slow) {
+                bool fast_work = false, slow_waiting = false;
+                for (const Req* r : s->pending) {
+                    const bool rs = slow(r);
+                    fast_work = fast_work || !rs;
+                    slow_waiting = slow_waiting || rs;
+                }
+                for (const Slot& o : s->slots) fast_work = fast_work || (o.busy && !o.slow);
+                if (fast_work && !slow_waiting) frac = share;
+            }
             sl.scratch = used;
             s->inflight_scratch += used;
             sl.busy = true;
             sl.t_launch = Clock::now();
             s->launches++;
             lk.unlock();
-            gz_status st = launch_batch(s, sl);
+            gz_status st = launch_batch(sl, frac);
             lk.lock();
             if (st != GZ_OK) {
                 auto now = Clock::now();
-                for (Req* r : sl.batch) { r->status = st; r->done = true; r->t_done = now; }
+                for (Req* r : sl.batch) finish(s, r, st, now);
                 s->inflight_scratch -= sl.scratch;
                 sl.batch.clear();
                 sl.busy = false;
-                s->cv_done.notify_all();
+                sl.slow = false;
             }
             progress = true;
         }
@@ -341,6 +367,10 @@ gz_status gz_server_replay(gz_server* s, const gz_plan* const* plans, const gz_g
     auto t0 = Clock::now();
     gz_status st = GZ_OK;
     if (fifo) {
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->whole = true;
+        }
         // plain baseline: one query per launch, strictly one at a time, in arrival order
         for (int64_t i = 0; i < nreq && st == GZ_OK; ++i) {
             arrive[i] = t0 + std::chrono::nanoseconds(arrival_ns[i]);
@@ -355,6 +385,8 @@ gz_status gz_server_replay(gz_server* s, const gz_plan* const* plans, const gz_g
         }
         // requests that arrived while earlier ones were served waited in the queue;
         // latency above is measured from each request's own arrival time
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->whole = false;
     } else {
         std::thread sub([&] {
             for (int64_t i = 0; i < nreq; ++i) {

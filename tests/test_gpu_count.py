@@ -233,6 +233,25 @@ def test_server_equals_alone():
     srv.close()
 
 
+def test_server_slow_share_equals_oracle():
+    """Every request classed slow (a tiny threshold): each runs alone on a small
+    share of the device while the others wait; the counts must still equal the
+    oracle's (the grid size never changes which work is done)."""
+    g = S.rmat(12, 16, 51)
+    G = gz.Graph.from_csr(g).orient()
+    names = ["triangle", "c4", "diamond", "k4", "k5", "chordal5"]
+    plans = [gz.Plan(n) for n in names]
+    want = [oracle_count(n, g) for n in names]
+    srv = gz.Server(max_inflight=2, max_batch=4, heavy_ms=1e-3, slow_share=0.05)
+    rng = np.random.default_rng(7)
+    pidx = rng.integers(0, len(names), 24).astype(np.int32)
+    arr = np.cumsum(rng.exponential(1e6, 24)).astype(np.int64)
+    counts, lat, stats = srv.replay(plans, [G], [1] * 24, arr, pidx, np.zeros(24, np.int32))
+    assert [int(c) for c in counts] == [want[i] for i in pidx]
+    assert stats["launches"] == 24  # every slow request alone in its launch
+    srv.close()
+
+
 def test_device_pointer_graph():
     import torch
     g = S.rmat(12, 16, 60)
