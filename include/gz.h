@@ -219,6 +219,8 @@ typedef struct {
     int64_t root_lo, root_hi; /* only roots (first scheduled vertex) in [lo, hi); hi < 0 = n */
     int block_warps;          /* warps per CTA, 0 = default */
     int chunk;                /* work units per queue pop, 0 = default or autotuned */
+    int64_t split_min;        /* loop-2 candidates from which a unit goes to the split pass, 0 = default or autotuned */
+    int64_t split_chunk;      /* loop-2 candidates per split-pass work item, 0 = default or autotuned */
 } gz_count_opts;
 
 /*
@@ -274,8 +276,10 @@ gz_status gz_scratch_bytes(const gz_plan* p, const gz_graph* g, int use_orientat
  * Batched counting: nq independent (plan, graph, use_orientation[i]) queries in
  * one call (no paper counterpart; the merged multi-pattern program of Sec. 3 is
  * the closest). The non-clique queries share one persistent launch over a device
- * work queue; clique queries take the clique kernels; both kinds overlap on a
- * small per-device stream pool and join `stream` before the call returns.
+ * work queue, each with the split thresholds gz_autotune chose for it (if any)
+ * and the launch shape tuned for the heaviest tuned query; clique queries take
+ * the clique kernels; both kinds overlap on a small per-device stream pool and
+ * join `stream` before the call returns.
  * out_counts[nq] (host) receives each query's exact count, identical to gz_count
  * of that query. Errors: GZ_EINVAL, GZ_ENOMEM, GZ_ECUDA.
  */
@@ -284,12 +288,21 @@ gz_status gz_count_batch(const gz_plan* const* plans, const gz_graph* const* gra
                          uint64_t* out_counts);
 
 /*
- * Autotuner: times candidate launch shapes (warps per CTA, units per queue pop)
- * for this (plan, graph) on the device and caches the fastest; later counts of
- * the same pair use it. Writes the choice to *block_warps and *chunk if not NULL.
+ * Autotuner (no paper counterpart): times candidate launch settings of the
+ * general kernel for this (plan, graph, view) with CUDA events on `stream`
+ * (median of 3 runs each) and keeps the fastest; later gz_count and
+ * gz_count_batch calls on the same program, graph and view use it. The search
+ * is one pass of coordinate descent from the defaults over the units per queue
+ * pop (1..16), the warps per CTA (4 or 8) and, for k >= 4, the split pass's
+ * thresholds: the loop-2 candidate count from which a work unit is deferred to
+ * the split pass (128..4096) and the candidates per split work item (64..512).
+ * The choices are written to the non-NULL outputs. The count never depends on
+ * them. Entries are keyed by the plan's program and a process-unique graph id,
+ * and a graph's entries are dropped when it is destroyed.
+ * Errors: as gz_count.
  */
 gz_status gz_autotune(const gz_plan* p, const gz_graph* g, int use_orientation, void* stream,
-                      int* block_warps, int* chunk);
+                      int* block_warps, int* chunk, int64_t* split_min, int64_t* split_chunk);
 
 /* ------------------------------------------------------------------ motifs */
 

@@ -49,7 +49,8 @@ class GraphStats(ctypes.Structure):
 
 class CountOpts(ctypes.Structure):
     _fields_ = [("use_orientation", ctypes.c_int), ("root_lo", ctypes.c_int64),
-                ("root_hi", ctypes.c_int64), ("block_warps", ctypes.c_int), ("chunk", ctypes.c_int)]
+                ("root_hi", ctypes.c_int64), ("block_warps", ctypes.c_int), ("chunk", ctypes.c_int),
+                ("split_min", ctypes.c_int64), ("split_chunk", ctypes.c_int64)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -97,7 +98,7 @@ def lib() -> ctypes.CDLL:
         "gz_scratch_bytes": [_P, _P, I, _u64p],
         "gz_count_noalloc": [_P, _P, I, _P, _u64p],
         "gz_count_batch": [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(I), I, _P, _u64p],
-        "gz_autotune": [_P, _P, I, _P, ctypes.POINTER(I), ctypes.POINTER(I)],
+        "gz_autotune": [_P, _P, I, _P, ctypes.POINTER(I), ctypes.POINTER(I), _i64p, _i64p],
         "gz_motif_patterns": [I, _u8p, I, ctypes.POINTER(I)],
         "gz_plan_create_measured": [I, _u8p, _P, I, _i64p, _i64p, I, _P, ctypes.POINTER(_P),
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
@@ -342,9 +343,9 @@ class Graph:
 # ------------------------------------------------------------------ counting
 
 def count(plan: Plan, graph: Graph, orientation: bool = False, root_lo: int = 0, root_hi: int = -1,
-          block_warps: int = 0, chunk: int = 0, stream=None) -> int:
+          block_warps: int = 0, chunk: int = 0, stream=None, split_min: int = 0, split_chunk: int = 0) -> int:
     """Exact number of vertex-induced instances of the plan's pattern."""
-    o = CountOpts(int(orientation), root_lo, root_hi, block_warps, chunk)
+    o = CountOpts(int(orientation), root_lo, root_hi, block_warps, chunk, split_min, split_chunk)
     out = ctypes.c_uint64()
     _check(lib().gz_count_ex(plan.handle, graph.handle, ctypes.byref(o), _stream(stream),
                              ctypes.byref(out)), "gz_count")
@@ -375,11 +376,14 @@ def count_batch(plans, graphs, orientation, stream=None) -> list[int]:
     return list(out)
 
 
-def autotune(plan: Plan, graph: Graph, orientation: bool = False, stream=None):
+def autotune(plan: Plan, graph: Graph, orientation: bool = False, stream=None) -> dict:
+    """gz_autotune: the launch settings chosen for (plan, graph, orientation)."""
     bw, ch = ctypes.c_int(), ctypes.c_int()
+    sm, sc = ctypes.c_int64(), ctypes.c_int64()
     _check(lib().gz_autotune(plan.handle, graph.handle, int(orientation), _stream(stream),
-                             ctypes.byref(bw), ctypes.byref(ch)), "gz_autotune")
-    return bw.value, ch.value
+                             ctypes.byref(bw), ctypes.byref(ch), ctypes.byref(sm), ctypes.byref(sc)),
+           "gz_autotune")
+    return {"block_warps": bw.value, "chunk": ch.value, "split_min": sm.value, "split_chunk": sc.value}
 
 
 def motif_patterns(k: int) -> list:

@@ -79,12 +79,15 @@ gz_status arena_reserve(Arena& a, uint64_t bytes) {
 
 // ------------------------------------------------------------ autotune cache
 
+// Tuned launch shape and split thresholds per (program, graph, view). Keys use
+// the plan's program hash and the graph's process-unique id, so a plan or graph
+// freed and another allocated at the same address never inherits an entry.
 struct TuneKey {
-    const gz_plan* p;
-    const gz_graph* g;
+    uint64_t plan;
+    uint64_t graph;
     int ori;
     bool operator<(const TuneKey& o) const {
-        return std::tie(p, g, ori) < std::tie(o.p, o.g, o.ori);
+        return std::tie(plan, graph, ori) < std::tie(o.plan, o.graph, o.ori);
     }
 };
 std::mutex g_tune_mu;
@@ -92,16 +95,20 @@ std::map<TuneKey, LaunchCfg>& tune_cache() {
     static std::map<TuneKey, LaunchCfg> m;
     return m;
 }
+std::atomic<uint64_t> g_graph_ids{1};
+
+bool tuned_cfg(const gz_plan* p, const gz_graph* g, int ori, LaunchCfg* out) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = tune_cache().find(TuneKey{p->hash, g->id, ori ? 1 : 0});
+    if (it == tune_cache().end()) return false;
+    *out = it->second;
+    return true;
+}
 
 void forget_graph(const gz_graph* g) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto& m = tune_cache();
-    for (auto it = m.begin(); it != m.end();) it = it->first.g == g ? m.erase(it) : std::next(it);
-}
-void forget_plan(const gz_plan* p) {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto& m = tune_cache();
-    for (auto it = m.begin(); it != m.end();) it = it->first.p == p ? m.erase(it) : std::next(it);
+    for (auto it = m.begin(); it != m.end();) it = it->first.graph == g->id ? m.erase(it) : std::next(it);
 }
 
 // ------------------------------------------------------------ device setup
@@ -400,6 +407,7 @@ gz_status gz_load_csr(const int64_t* row_ptr, const int32_t* col_idx, int64_t n,
     if (!g) { set_error("gz_load_csr: out of host memory"); return GZ_ENOMEM; }
     g->n = n;
     g->nnz = nnz;
+    g->id = g_graph_ids.fetch_add(1);
     cudaGetDevice(&g->device);
     cudaError_t e = cudaSuccess;
     if (device_ptrs) {
@@ -685,9 +693,7 @@ gz_status gz_plan_describe(const gz_plan* p, char* buf, int cap) {
 }
 
 void gz_plan_destroy(gz_plan* p) {
-    if (!p) return;
-    forget_plan(p);
-    delete p;
+    delete p;  // tuned entries are keyed by the program, which other plans may share
 }
 
 gz_status gz_count_ex(const gz_plan* p, const gz_graph* g, const gz_count_opts* opts, void* stream,
@@ -706,13 +712,11 @@ gz_status gz_count_ex(const gz_plan* p, const gz_graph* g, const gz_count_opts* 
     gz_status st = prepare_query(p, g, o.use_orientation, o.root_lo, o.root_hi, s, q);
     if (st != GZ_OK) return st;
     LaunchCfg cfg = default_cfg();
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = tune_cache().find(TuneKey{p, g, o.use_orientation ? 1 : 0});
-        if (it != tune_cache().end()) cfg = it->second;
-    }
+    tuned_cfg(p, g, o.use_orientation, &cfg);
     if (o.block_warps > 0) cfg.block_warps = std::min(8, o.block_warps);
     if (o.chunk > 0) cfg.chunk = o.chunk;
+    if (o.split_min > 0) cfg.split_min = o.split_min;
+    if (o.split_chunk > 0) cfg.split_chunk = o.split_chunk;
     *out_count = 0;
     if (q.unit_hi <= q.unit_lo) return GZ_OK;
     return run_queries(&q, 1, cfg, s, out_count);
@@ -763,8 +767,23 @@ gz_status gz_count_batch(const gz_plan* const* plans, const gz_graph* const* gra
     });
     std::vector<Query> sorted(nq);
     for (int i = 0; i < nq; ++i) sorted[i] = qs[idx[i]];
-    std::vector<uint64_t> res(nq, 0);
+    // tuned queries keep their own split thresholds; the launch takes the warps
+    // per CTA and units per pop tuned for the heaviest tuned query
     LaunchCfg cfg = default_cfg();
+    bool shape = false;
+    for (int i = 0; i < nq; ++i) {
+        LaunchCfg t;
+        const int j = idx[i];
+        if (!tuned_cfg(plans[j], graphs[j], use_orientation ? use_orientation[j] : 0, &t)) continue;
+        sorted[i].split_min = t.split_min;
+        sorted[i].split_chunk = t.split_chunk;
+        if (!shape) {
+            cfg.block_warps = t.block_warps;
+            cfg.chunk = t.chunk;
+            shape = true;
+        }
+    }
+    std::vector<uint64_t> res(nq, 0);
     gz_status st = run_queries(sorted.data(), nq, cfg, s, res.data());
     if (st != GZ_OK) return st;
     for (int i = 0; i < nq; ++i) out_counts[idx[i]] = res[i];
@@ -772,36 +791,78 @@ gz_status gz_count_batch(const gz_plan* const* plans, const gz_graph* const* gra
 }
 
 gz_status gz_autotune(const gz_plan* p, const gz_graph* g, int use_orientation, void* stream,
-                      int* block_warps, int* chunk) {
+                      int* block_warps, int* chunk, int64_t* split_min, int64_t* split_chunk) {
+    GZ_RANGE("gz_autotune");
     if (!p || !check_graph(g, "gz_autotune")) return GZ_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     Query q{};
     gz_status st = prepare_query(p, g, use_orientation, 0, -1, s, q);
     if (st != GZ_OK) return st;
-    const int bw_c[] = {2, 4, 8};
-    const int ch_c[] = {1, 4, 16};
-    LaunchCfg best = default_cfg();
-    double best_t = 1e300;
-    if (q.unit_hi > q.unit_lo) {
-        for (int bw : bw_c)
-            for (int ch : ch_c) {
-                LaunchCfg c;
-                c.block_warps = bw;
-                c.chunk = ch;
-                uint64_t cnt = 0;
-                auto t0 = std::chrono::steady_clock::now();
-                st = run_queries(&q, 1, c, s, &cnt);
-                double t = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-                if (st != GZ_OK) return st;
-                if (t < best_t) { best_t = t; best = c; }
-            }
+    // device time of one count with cfg (CUDA events on the stream), the median
+    // of reps runs after one untimed run
+    cudaEvent_t ev[2];
+    if (cudaEventCreate(&ev[0]) != cudaSuccess) return cuda_fail(cudaGetLastError(), "autotune: event");
+    if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+        cudaEventDestroy(ev[0]);
+        return cuda_fail(cudaGetLastError(), "autotune: event");
     }
+    auto timed = [&](const LaunchCfg& c, double* ms) -> gz_status {
+        uint64_t cnt = 0;
+        gz_status r = run_queries(&q, 1, c, s, &cnt);
+        std::vector<double> t;
+        for (int rep = 0; rep < 3 && r == GZ_OK; ++rep) {
+            cudaEventRecord(ev[0], s);
+            r = run_queries(&q, 1, c, s, &cnt);
+            cudaEventRecord(ev[1], s);
+            cudaEventSynchronize(ev[1]);
+            float x = 0.f;
+            cudaEventElapsedTime(&x, ev[0], ev[1]);
+            t.push_back(x);
+        }
+        if (r != GZ_OK) return r;
+        std::sort(t.begin(), t.end());
+        *ms = t[t.size() / 2];
+        return GZ_OK;
+    };
+    // coordinate descent from the defaults: units per queue pop, warps per
+    // CTA, then the split pass's thresholds (plans with k >= 4 only)
+    LaunchCfg best = default_cfg();
+    double best_ms = 0.0;
+    // oriented cliques run on the clique kernels, which take none of these settings
+    const bool clique = clique_eligible(*q.prog, *p, *q.view) && q.view->max_out <= kCliqueLongOut;
+    if (q.unit_hi > q.unit_lo && !clique) {
+        st = timed(best, &best_ms);
+        auto try_values = [&](auto set, std::initializer_list<int64_t> values) {
+            for (int64_t v : values) {
+                if (st != GZ_OK) return;
+                LaunchCfg c = best;
+                set(c, v);
+                double ms = 0.0;
+                st = timed(c, &ms);
+                if (st == GZ_OK && ms < best_ms) {
+                    best_ms = ms;
+                    best = c;
+                }
+            }
+        };
+        try_values([](LaunchCfg& c, int64_t v) { c.chunk = (int)v; }, {1, 2, 8, 16});
+        try_values([](LaunchCfg& c, int64_t v) { c.block_warps = (int)v; }, {4});
+        if (p->k >= 4) {
+            try_values([](LaunchCfg& c, int64_t v) { c.split_min = v; }, {128, 256, 1024, 4096});
+            try_values([](LaunchCfg& c, int64_t v) { c.split_chunk = v; }, {64, 128, 512});
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (st != GZ_OK) return st;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        tune_cache()[TuneKey{p, g, use_orientation ? 1 : 0}] = best;
+        tune_cache()[TuneKey{p->hash, g->id, use_orientation ? 1 : 0}] = best;
     }
     if (block_warps) *block_warps = best.block_warps;
     if (chunk) *chunk = best.chunk;
+    if (split_min) *split_min = best.split_min;
+    if (split_chunk) *split_chunk = best.split_chunk;
     return GZ_OK;
 }
 

@@ -62,6 +62,8 @@ struct KQ {
     int64_t buf_cap[GZ_MAXBUF];
     int64_t hash_off;      // per-warp hash table for a fixed operand too long for shared memory
     int32_t hash_log2;     // its slot count is 1 << hash_log2 (0: none)
+    int64_t split_min;     // loop-2 candidates from which a unit goes to the split pass
+    int64_t split_chunk;   // loop-2 candidates per split-pass work item
 };
 
 constexpr int kGlobalHashLog2 = 17;  // largest per-warp hash table in scratch (slots)
@@ -94,21 +96,23 @@ uint64_t scratch_layout(const GzProg& p, const gz_graph& g, const GzView& v, KQ*
 }
 
 // Splitting of heavy units. A unit whose loop-2 candidate list holds at least
-// LaunchCfg::split_min vertices is not run by the warp that popped it: the first
-// pass records it (launch-space unit index and candidate count), a one-CTA scan
-// turns the records into chunks of LaunchCfg::split_chunk candidates, and a
-// second pass hands the chunks to warps, each recomputing loop 1 and walking its
-// chunk of loop 2. A hub edge then spreads over many warps instead of holding one.
+// its query's split_min vertices is not run by the warp that popped it: the
+// first pass records it (launch-space unit index, candidate count and the
+// query's split_chunk), a one-CTA scan turns the records into chunks of
+// split_chunk candidates, and a second pass hands the chunks to warps, each
+// recomputing loop 1 and walking its chunk of loop 2. A hub edge then spreads
+// over many warps instead of holding one. Both thresholds are per query (the
+// autotuner picks them).
 struct Deferred {
-    int64_t unit;  // launch-space unit index
-    int64_t n2;    // loop-2 candidates
+    int64_t unit;   // launch-space unit index
+    int64_t n2;     // loop-2 candidates
+    int64_t chunk;  // candidates per split-pass work item
 };
 
 struct DeferCtl {
     Deferred* list;              // NULL: no deferral
     unsigned long long* count;   // records written (may exceed cap)
     int64_t cap;
-    int64_t min_n2;              // loop-2 candidates from which a unit is deferred
 };
 
 // Number of elements of sorted L[0, n) that are < beta (warp-cooperative
@@ -576,7 +580,7 @@ __device__ void last_level_flat(const KQ& q, const GzOp& op, WarpState& ws, List
 }
 
 // Runs one unit (e0, e1), loop 2 restricted to candidates [lo2, hi2) (hi2 < 0:
-// all). With df.list set, a unit with at least df.min_n2 loop-2 candidates is
+// all). With df.list set, a unit with at least q.split_min loop-2 candidates is
 // recorded for the split pass instead (u = its launch-space index).
 __device__ void process_unit(const KQ& q, int64_t unit, WarpState& ws, int32_t* scratch,
                              int32_t* sm, int lane, unsigned long long& acc, int* status,
@@ -597,12 +601,12 @@ __device__ void process_unit(const KQ& q, int64_t unit, WarpState& ws, int32_t* 
     run_level(q, 1, ws, scratch, lane, acc, status);
     if (k == 3) return;
     const ListRef c2 = cand_list(q, 2, ws, scratch, lane);
-    if (df && df->list && c2.n >= df->min_n2) {
+    if (df && df->list && c2.n >= q.split_min) {
         unsigned long long slot = 0;
         if (lane == 0) slot = atomicAdd(df->count, 1ull);
         slot = __shfl_sync(kFull, slot, 0);
         if ((int64_t)slot < df->cap) {
-            if (lane == 0) df->list[slot] = Deferred{u, c2.n};
+            if (lane == 0) df->list[slot] = Deferred{u, c2.n, q.split_chunk};
             __syncwarp();
             return;
         }
@@ -702,14 +706,13 @@ __global__ void __launch_bounds__(256, 2) k_enumerate(const KQ* __restrict__ qs,
 // the min(count, cap) records of the first pass; prefix[n] = all chunks. One CTA.
 __global__ void __launch_bounds__(1024) k_split_scan(const Deferred* __restrict__ dl,
                                                      const unsigned long long* __restrict__ dcount,
-                                                     int64_t cap, int64_t chunk,
-                                                     int64_t* __restrict__ prefix) {
+                                                     int64_t cap, int64_t* __restrict__ prefix) {
     __shared__ int64_t part[1024];
     const int64_t n = (int64_t)*dcount < cap ? (int64_t)*dcount : cap;
     const int64_t per = (n + 1023) / 1024;
     const int64_t b = threadIdx.x * per, e = b + per < n ? b + per : n;
     int64_t sum = 0;
-    for (int64_t i = b; i < e; ++i) sum += (dl[i].n2 + chunk - 1) / chunk;
+    for (int64_t i = b; i < e; ++i) sum += (dl[i].n2 + dl[i].chunk - 1) / dl[i].chunk;
     part[threadIdx.x] = sum;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -725,7 +728,7 @@ __global__ void __launch_bounds__(1024) k_split_scan(const Deferred* __restrict_
     int64_t run = part[threadIdx.x];
     for (int64_t i = b; i < e; ++i) {
         prefix[i] = run;
-        run += (dl[i].n2 + chunk - 1) / chunk;
+        run += (dl[i].n2 + dl[i].chunk - 1) / dl[i].chunk;
     }
 }
 
@@ -735,7 +738,6 @@ __global__ void __launch_bounds__(256, 2) k_enumerate_split(const KQ* __restrict
                                                          const unsigned long long* __restrict__ dcount,
                                                          int64_t cap,
                                                          const int64_t* __restrict__ prefix,
-                                                         int64_t chunk,
                                                          unsigned long long* __restrict__ work,
                                                          unsigned long long* __restrict__ counts,
                                                          int* __restrict__ status,
@@ -762,7 +764,7 @@ __global__ void __launch_bounds__(256, 2) k_enumerate_split(const KQ* __restrict
             if (prefix[mid] <= (int64_t)t) lo = mid; else hi = mid - 1;
         }
         const Deferred rec = dl[lo];
-        const int64_t c0 = ((int64_t)t - prefix[lo]) * chunk;
+        const int64_t c0 = ((int64_t)t - prefix[lo]) * rec.chunk;
         const int64_t u = rec.unit;
         if (cur < 0 || u < qs[cur].unit_begin || u >= qs[cur].unit_begin + qs[cur].unit_count) {
             if (cur >= 0) {
@@ -779,7 +781,7 @@ __global__ void __launch_bounds__(256, 2) k_enumerate_split(const KQ* __restrict
         }
         const KQ& q = qs[cur];
         process_unit(q, q.unit_lo + (u - q.unit_begin), ws, my, sm, lane, acc, status, c0,
-                     c0 + chunk);
+                     c0 + rec.chunk);
     }
     if (cur >= 0) {
         unsigned long long s = warp_sum(acc);
@@ -826,7 +828,6 @@ __global__ void __launch_bounds__(256, 2) k_enumerate_split_one(const __grid_con
                                                              const unsigned long long* __restrict__ dcount,
                                                              int64_t cap,
                                                              const int64_t* __restrict__ prefix,
-                                                             int64_t chunk,
                                                              unsigned long long* __restrict__ work,
                                                              unsigned long long* __restrict__ count,
                                                              int* __restrict__ status,
@@ -851,15 +852,19 @@ __global__ void __launch_bounds__(256, 2) k_enumerate_split_one(const __grid_con
             const int64_t mid = (lo + hi + 1) >> 1;
             if (prefix[mid] <= (int64_t)t) lo = mid; else hi = mid - 1;
         }
-        const int64_t c0 = ((int64_t)t - prefix[lo]) * chunk;
-        process_unit(q, q.unit_lo + dl[lo].unit, ws, my, sm, lane, acc, status, c0, c0 + chunk);
+        const Deferred rec = dl[lo];
+        const int64_t c0 = ((int64_t)t - prefix[lo]) * rec.chunk;
+        process_unit(q, q.unit_lo + rec.unit, ws, my, sm, lane, acc, status, c0, c0 + rec.chunk);
     }
     unsigned long long s = warp_sum(acc);
     if (lane == 0 && s) atomicAdd(count, s);
 }
 
-void fill_kq(const Query& Q, KQ& k, uint64_t* words_out) {
+void fill_kq(const Query& Q, const LaunchCfg& cfg, KQ& k, uint64_t* words_out) {
     memset(&k, 0, sizeof(KQ));
+    k.split_min = Q.split_min > 0 ? Q.split_min : cfg.split_min;
+    k.split_chunk = Q.split_chunk > 0 ? Q.split_chunk : cfg.split_chunk;
+    if (k.split_chunk < 1) k.split_chunk = 1;
     k.prog = *Q.prog;
     const GzView& v = *Q.view;
     k.rp = v.rp; k.col = v.col; k.drp = v.dag_rp; k.dcol = v.dag_col;
@@ -948,7 +953,7 @@ gz_status count_one_in_region(const Query& Q, const LaunchCfg& cfg, cudaStream_t
                               uint64_t scratch_bytes, bool split, uint64_t* out_count) {
     KQ k;
     uint64_t words = 0;
-    fill_kq(Q, k, &words);
+    fill_kq(Q, cfg, k, &words);
     const int64_t total = Q.unit_hi - Q.unit_lo;
     *out_count = 0;
     if (total <= 0) return GZ_OK;
@@ -981,16 +986,15 @@ gz_status count_one_in_region(const Query& Q, const LaunchCfg& cfg, cudaStream_t
     const int chunk = cfg.chunk > 0 ? cfg.chunk : 1;
     cudaError_t e = cudaMemsetAsync(region, 0, kRegionHeader, s);
     if (e == cudaSuccess) {
-        DeferCtl df{dl, hdr + 4, cap, cfg.split_min};
+        DeferCtl df{dl, hdr + 4, cap};
         k_enumerate_one<<<blocks, bw * 32, cta_smem(bw), s>>>(k, total, chunk, hdr, hdr + 1, status, scratch,
                                                              (int64_t)words, df);
         GZ_COUNT_LAUNCH();
         if (split) {
-            k_split_scan<<<1, 1024, 0, s>>>(dl, hdr + 4, cap, cfg.split_chunk, prefix);
+            k_split_scan<<<1, 1024, 0, s>>>(dl, hdr + 4, cap, prefix);
             GZ_COUNT_LAUNCH();
-            k_enumerate_split_one<<<blocks, bw * 32, cta_smem(bw), s>>>(k, dl, hdr + 4, cap, prefix,
-                                                                       cfg.split_chunk, hdr + 3, hdr + 1,
-                                                                       status, scratch, (int64_t)words);
+            k_enumerate_split_one<<<blocks, bw * 32, cta_smem(bw), s>>>(k, dl, hdr + 4, cap, prefix, hdr + 3,
+                                                                       hdr + 1, status, scratch, (int64_t)words);
             GZ_COUNT_LAUNCH();
         }
         e = cudaGetLastError();
@@ -1052,7 +1056,7 @@ gz_status count_launch(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream
         const Query& Q = qs[i];
         KQ& k = h[i];
         uint64_t w = 0;
-        fill_kq(Q, k, &w);
+        fill_kq(Q, cfg, k, &w);
         k.unit_begin = total;
         k.out_slot = Q.out_slot >= 0 ? Q.out_slot : i;
         total += k.unit_count;
@@ -1085,16 +1089,16 @@ gz_status count_launch(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream
     if (e == cudaSuccess) {
         int blocks = warps / cfg.block_warps;
         if (cfg.grid_frac < 1.0) blocks = std::max(1, (int)(blocks * cfg.grid_frac));
-        DeferCtl df{split ? dl : nullptr, work + 2, cap, cfg.split_min};
+        DeferCtl df{split ? dl : nullptr, work + 2, cap};
         k_enumerate<<<blocks, cfg.block_warps * 32, cta_smem(cfg.block_warps), s>>>(
             d, nq, total, cfg.chunk > 0 ? cfg.chunk : 1, work, d_counts, d_status,
             reinterpret_cast<int32_t*>(scratch), (int64_t)words, df);
         GZ_COUNT_LAUNCH();
         if (split) {
-            k_split_scan<<<1, 1024, 0, s>>>(dl, work + 2, cap, cfg.split_chunk, prefix);
+            k_split_scan<<<1, 1024, 0, s>>>(dl, work + 2, cap, prefix);
             GZ_COUNT_LAUNCH();
             k_enumerate_split<<<blocks, cfg.block_warps * 32, cta_smem(cfg.block_warps), s>>>(
-                d, nq, dl, work + 2, cap, prefix, cfg.split_chunk, work + 1, d_counts, d_status,
+                d, nq, dl, work + 2, cap, prefix, work + 1, d_counts, d_status,
                 reinterpret_cast<int32_t*>(scratch), (int64_t)words);
             GZ_COUNT_LAUNCH();
         }

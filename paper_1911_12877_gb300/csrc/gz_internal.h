@@ -54,6 +54,7 @@ struct GzProg {
 
 // Host-side plan (opaque gz_plan).
 struct gz_plan {
+    uint64_t hash;                     // of (k, adj, order): identifies the program for caches
     int k;
     uint8_t adj[GZ_MAX_K * GZ_MAX_K];  // pattern, labels
     int32_t order[GZ_MAX_K];           // schedule (labels)
@@ -103,6 +104,7 @@ struct GzView {
 };
 
 struct gz_graph {
+    uint64_t id = 0;       // unique in the process (never reused), for caches
     int64_t n = 0, nnz = 0, max_deg = 0;
     int device = 0;
     GzView orig;
@@ -182,6 +184,8 @@ struct Query {
     int64_t root_lo = 0, root_hi = -1;  // the roots those units belong to (hi < 0: n)
     int64_t min_root_out = 0;  // > 0: only roots with at least this out-degree
     int out_slot = -1;         // count slot in the launch's count array (-1: its index)
+    int64_t split_min = 0;     // split thresholds of this query (0: the launch's)
+    int64_t split_chunk = 0;
 };
 struct LaunchCfg {
     int block_warps = 8;     // warps per CTA

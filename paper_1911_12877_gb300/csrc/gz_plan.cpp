@@ -415,6 +415,12 @@ gz_status make_plan(int k, const uint8_t* adj, const int32_t* forced_order, gz_p
     memcpy(pl->bp, bp, sizeof(int32_t) * k);
     pl->aut_size = aut.size();
     pl->est_cost = cost;
+    uint64_t h = 1469598103934665603ull;  // FNV-1a over k, adjacency and schedule
+    auto mix = [&h](uint64_t x) { h = (h ^ x) * 1099511628211ull; };
+    mix((uint64_t)k);
+    for (int i = 0; i < k * k; ++i) mix(pl->adj[i]);
+    for (int i = 0; i < k; ++i) mix((uint64_t)(uint32_t)pl->order[i]);
+    pl->hash = h;
     if (!c.compile(pl->prog)) {
         delete pl;
         return GZ_EINVAL;

@@ -150,14 +150,32 @@ def test_launch_shapes_do_not_change_counts(bw, chunk):
         assert gz.count(p, G, True, block_warps=bw, chunk=chunk) == oracle_count(name, g)
 
 
-def test_autotune_keeps_count():
+@pytest.mark.parametrize("name", ["k4", "diamond", "c4"])
+def test_autotune_keeps_count(name):
     g = S.rmat(13, 16, 11)
     G = gz.Graph.from_csr(g).orient()
-    p = gz.Plan("k4")
-    want = gz.count(p, G, True)
-    bw, ch = gz.autotune(p, G, True)
-    assert bw in (2, 4, 8) and ch in (1, 4, 16)
-    assert gz.count(p, G, True) == want == oracle_count("k4", g)
+    p = gz.Plan(name)
+    want = oracle_count(name, g)
+    assert gz.count(p, G, True) == want
+    t = gz.autotune(p, G, True)
+    assert t["block_warps"] in (4, 8) and t["chunk"] in (1, 2, 4, 8, 16)
+    assert t["split_min"] in (128, 256, 512, 1024, 4096) and t["split_chunk"] in (64, 128, 256, 512)
+    assert gz.count(p, G, True) == want  # single count with the tuned settings
+    # a batch with the tuned query beside untuned ones
+    q = gz.Plan("triangle")
+    assert gz.count_batch([p, q, p], [G, G, G], [True, False, True]) == [want, oracle_count("triangle", g), want]
+
+
+def test_split_thresholds_do_not_change_counts():
+    """Tuned split thresholds per query: with every unit deferred (threshold 1)
+    and one-candidate work items the counts stay the oracle's."""
+    g = S.rmat(12, 16, 12)
+    G = gz.Graph.from_csr(g).orient()
+    for name in ["diamond", "c4", "house", "chordal5"]:
+        p = gz.Plan(name)
+        want = oracle_count(name, g)
+        assert gz.count(p, G, True, split_min=1, split_chunk=1) == want, name
+        assert gz.count(p, G, True, split_min=1 << 40, split_chunk=512) == want, name
 
 
 def test_batch_equals_alone():
