@@ -781,7 +781,9 @@ def run_motifs(args, dist, world, rank, local):
     """Motif counting (Sec. 7.1-7.2, Table 2): every connected 3-, 4- and 5-vertex
     pattern counted on a seeded graph of the size of the paper's smallest dataset
     (ER with 3,264 vertices and ~4,536 edges, CiteSeer's counts; seed 7), and on
-    R-MAT scale 12 ef 8 for a skewed one; each motif size in one batched call."""
+    R-MAT scale 12 ef 8 for a skewed one; each motif size as one merged program
+    (gz_count_merged, the path of gz_count_motifs), against the same plans as
+    separate programs in one batched call."""
     import torch
     import paper_1911_12877_gb300 as gz
     import synthetic as S
@@ -795,11 +797,21 @@ def run_motifs(args, dist, world, rank, local):
     for gname, g in graphs.items():
         G = gz.Graph.from_csr(g).orient()
         for k in (3, 4, 5):
-            counts, ms = _time_counts(lambda: gz.count_motifs(G, k, orientation=True), args.steps, stream)
-            res[f"{gname}/motif{k}"] = {"patterns": len(counts), "sum": int(sum(counts)), **_summary(ms)}
+            # the same plans as one merged program and as separate programs in one
+            # batched call; gz_count_motifs (planning included) must agree
+            plans = [gz.Plan(a) for a in gz.motif_patterns(k)]
+            counts, ms = _time_counts(lambda: gz.count_merged(plans, G, orientation=True), args.steps, stream)
+            sep, ms_s = _time_counts(lambda: gz.count_batch(plans, [G] * len(plans), [True] * len(plans)),
+                                     args.steps, stream)
+            if sep != counts or gz.count_motifs(G, k, orientation=True) != counts:
+                raise SystemExit(f"{gname} motif-{k}: merged and separate programs disagree")
+            res[f"{gname}/motif{k}"] = {"patterns": len(counts), "sum": int(sum(counts)), **_summary(ms),
+                                        "separate_programs_median_ms": round(statistics.median(ms_s), 4),
+                                        "merged_speedup": round(statistics.median(ms_s) / statistics.median(ms), 3)}
             total_ms += statistics.median(ms)
     launches = gz.kernel_launches() - l0
-    return _line("motif-3/4/5 count time (sum of medians)", total_ms, "ms", args, world, total_ms,
+    return _line("motif-3/4/5 count time, merged programs (sum of medians)", total_ms, "ms", args, world,
+                 total_ms,
                  {"workload": "all connected 3-, 4- and 5-vertex patterns (2 + 6 + 21) on an ER graph "
                               "of CiteSeer's size (3,264 V, ~4,536 E, seed 7) and on R-MAT 12 ef 8",
                   "n_graphs": len(graphs)},

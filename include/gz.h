@@ -304,6 +304,22 @@ gz_status gz_count_batch(const gz_plan* const* plans, const gz_graph* const* gra
 gz_status gz_autotune(const gz_plan* p, const gz_graph* g, int use_orientation, void* stream,
                       int* block_warps, int* chunk, int64_t* split_min, int64_t* split_chunk);
 
+/*
+ * Merged multi-pattern counting (Sec. 3: with several patterns GraphZero merges
+ * their schedules into one mining program; Sec. 7.2 counts motifs that way):
+ * the exact count of each of the np plans' patterns in one graph, written to
+ * out_counts[np] (host). The plans whose loop-1 candidates come from the same
+ * lists (out-lists or whole lists) form one merged program: their loop-1 set
+ * operations that build candidate sets are deduplicated, and one kernel walks
+ * the edges (e0, e1) once, computing those shared sets once per edge and then
+ * running each plan's remaining loops against them; a plan's edges with many
+ * loop-2 candidates go to a split pass as in gz_count. Oriented k-cliques
+ * (use_orientation = 1) run on the bitset clique kernels beside it. The counts
+ * equal gz_count's. Errors: GZ_EINVAL, GZ_ENOMEM, GZ_ECUDA.
+ */
+gz_status gz_count_merged(const gz_plan* const* plans, int np, const gz_graph* g, int use_orientation,
+                          void* stream, uint64_t* out_counts);
+
 /* ------------------------------------------------------------------ motifs */
 
 #define GZ_MOTIF_MAX_K 7
@@ -322,7 +338,7 @@ gz_status gz_motif_patterns(int k, uint8_t* adjs, int cap, int* count);
 /*
  * Motif counting: the exact vertex-induced count of every pattern of
  * gz_motif_patterns(k), in that order, each planned like gz_plan_create and all
- * counted in one gz_count_batch call. counts must hold the number of patterns
+ * counted in one merged program (gz_count_merged). counts must hold the number of patterns
  * (*count receives it; with counts NULL only *count is written).
  * Errors: GZ_EINVAL (k out of range, cap too small), GZ_ENOMEM, GZ_ECUDA.
  */

@@ -29,7 +29,7 @@ EXPORTS = [
     "gz_plan_schedules", "gz_plan_describe", "gz_plan_destroy", "gz_count", "gz_count_ex", "gz_scratch_bytes",
     "gz_count_batch", "gz_count_noalloc", "gz_autotune", "gz_server_create", "gz_server_submit", "gz_server_wait",
     "gz_server_replay", "gz_server_destroy", "gz_last_error", "gz_version", "gz_kernel_launches",
-    "gz_allocations",
+    "gz_allocations", "gz_count_merged",
     "gz_motif_patterns", "gz_count_motifs", "gz_plan_create_measured", "gz_schedule_times",
 ]
 
@@ -98,6 +98,7 @@ def lib() -> ctypes.CDLL:
         "gz_scratch_bytes": [_P, _P, I, _u64p],
         "gz_count_noalloc": [_P, _P, I, _P, _u64p],
         "gz_count_batch": [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(I), I, _P, _u64p],
+        "gz_count_merged": [ctypes.POINTER(_P), I, _P, I, _P, _u64p],
         "gz_autotune": [_P, _P, I, _P, ctypes.POINTER(I), ctypes.POINTER(I), _i64p, _i64p],
         "gz_motif_patterns": [I, _u8p, I, ctypes.POINTER(I)],
         "gz_plan_create_measured": [I, _u8p, _P, I, _i64p, _i64p, I, _P, ctypes.POINTER(_P),
@@ -374,6 +375,17 @@ def count_batch(plans, graphs, orientation, stream=None) -> list[int]:
     out = (ctypes.c_uint64 * nq)()
     _check(lib().gz_count_batch(P, G, O, nq, _stream(stream), out), "gz_count_batch")
     return list(out)
+
+
+def count_merged(plans, graph: Graph, orientation: bool = False, stream=None) -> list[int]:
+    """gz_count_merged: the counts of several patterns in one graph, counted by one
+    merged program (shared loop-1 sets, one pass over the edges)."""
+    n = len(plans)
+    P = (_P * max(n, 1))(*[p.handle for p in plans])
+    out = np.zeros(max(n, 1), dtype=np.uint64)
+    _check(lib().gz_count_merged(P, n, graph.handle, int(orientation), _stream(stream),
+                                 out.ctypes.data_as(_u64p)), "gz_count_merged")
+    return [int(x) for x in out[:n]]
 
 
 def autotune(plan: Plan, graph: Graph, orientation: bool = False, stream=None) -> dict:

@@ -790,6 +790,108 @@ gz_status gz_count_batch(const gz_plan* const* plans, const gz_graph* const* gra
     return GZ_OK;
 }
 
+gz_status gz_count_merged(const gz_plan* const* plans, int np, const gz_graph* g, int use_orientation,
+                          void* stream, uint64_t* out_counts) {
+    GZ_RANGE("gz_count_merged");
+    if (np < 0 || (np > 0 && (!plans || !out_counts)) || !check_graph(g, "gz_count_merged")) {
+        set_error("gz_count_merged: bad arguments");
+        return GZ_EINVAL;
+    }
+    if (np == 0) return GZ_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<Query> qs(np);
+    for (int i = 0; i < np; ++i) {
+        if (!plans[i]) { set_error("gz_count_merged: NULL plan at %d", i); return GZ_EINVAL; }
+        gz_status st = prepare_query(plans[i], g, use_orientation, 0, -1, s, qs[i]);
+        if (st != GZ_OK) return st;
+    }
+    // oriented cliques keep the bitset kernels; the other plans form merged programs
+    std::vector<int> gen_idx, cliq_idx;
+    std::vector<Query> cliq;
+    for (int i = 0; i < np; ++i) {
+        if (qs[i].unit_hi <= qs[i].unit_lo) continue;
+        if (clique_eligible(*qs[i].prog, *qs[i].plan, *qs[i].view) && qs[i].view->max_out <= kCliqueLongOut) {
+            cliq.push_back(qs[i]);
+            cliq_idx.push_back(i);
+        } else {
+            gen_idx.push_back(i);
+        }
+    }
+    std::vector<GzMerged> groups;
+    gz_status st = merge_plans(plans, gen_idx.data(), (int)gen_idx.size(), groups);
+    if (st != GZ_OK) return st;
+    const GzView* v = use_orientation ? &g->ori : &g->orig;
+    const LaunchCfg cfg = default_cfg();
+    uint64_t gwords = 0, gmeta = 0;
+    for (const GzMerged& m : groups) {
+        gwords = std::max(gwords, merged_scratch_words(m, *g, *v));
+        gmeta = std::max(gmeta, merged_meta_bytes(m, m.unit_dag ? v->dag_nnz : g->nnz));
+    }
+    auto a256 = [](uint64_t x) { return (x + 255) & ~255ull; };
+    // arena: counts [np], status, clique counts [nc], clique work [kCliqueWork nc] |
+    // merged metadata | merged scratch | clique metadata | clique scratch
+    const size_t nc = cliq.size();
+    const size_t hwords = (size_t)np + 1 + nc + kCliqueWork * nc;
+    const uint64_t head = a256(sizeof(unsigned long long) * hwords);
+    const uint64_t gscr = a256((uint64_t)resident_warps(cfg) * gwords * sizeof(int32_t));
+    const uint64_t cmeta = a256(mixed_meta_bytes(cliq.data(), (int)nc));
+    const uint64_t cscr = a256(mixed_scratch_bytes(cliq.data(), (int)nc, cfg));
+    Arena& a = arena();
+    std::lock_guard<std::mutex> lk(a.mu);
+    st = arena_reserve(a, head + a256(gmeta) + gscr + cmeta + cscr);
+    if (st != GZ_OK) return st;
+    char* base = reinterpret_cast<char*>(a.ptr);
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(base);
+    int* d_status = reinterpret_cast<int*>(d + np);
+    char* gm = base + head;
+    char* gs = gm + a256(gmeta);
+    char* cm = gs + gscr;
+    char* cs = cm + cmeta;
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned long long) * hwords, s);
+    if (e != cudaSuccess) return cuda_fail(e, "gz_count_merged: memset");
+    // the merged programs on a pool stream, the cliques forked from s beside them
+    cudaStream_t* pool = nullptr;
+    cudaStream_t t = s;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (!groups.empty() && nc > 0 && stream_pool(&pool) == GZ_OK &&
+        cudaEventCreateWithFlags(&ev0, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventCreateWithFlags(&ev1, cudaEventDisableTiming) == cudaSuccess) {
+        t = pool[kPool - 1];
+        cudaEventRecord(ev0, s);
+        cudaStreamWaitEvent(t, ev0, 0);
+    }
+    for (const GzMerged& m : groups) {
+        if (st != GZ_OK) break;
+        st = count_merged(m, g, v, cfg, t, d, d_status, gs, gscr, gm, gmeta);
+    }
+    if (st == GZ_OK && nc > 0)  // clique counts land in their own slots, moved to their plans' below
+        st = launch_mixed(cliq.data(), (int)nc, cfg, s, d + np + 1, d_status, d + np + 1 + nc, cs, cscr, cm,
+                          cmeta, true);
+    if (ev1) {
+        cudaEventRecord(ev1, t);
+        cudaStreamWaitEvent(s, ev1, 0);
+    }
+    std::vector<unsigned long long> h(hwords);
+    if (st == GZ_OK) {
+        e = cudaMemcpyAsync(h.data(), d, sizeof(unsigned long long) * hwords, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_fail(e, "gz_count_merged");
+    } else {
+        cudaStreamSynchronize(s);
+        if (t != s) cudaStreamSynchronize(t);
+    }
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    if (st != GZ_OK) return st;
+    if (*reinterpret_cast<int*>(&h[np]) != 0) {
+        set_error("gz_count_merged: a scratch buffer overflowed (planner capacity bug)");
+        return GZ_EOVERFLOW;
+    }
+    for (int i = 0; i < np; ++i) out_counts[i] = h[i];
+    for (size_t c = 0; c < nc; ++c) out_counts[cliq_idx[c]] = h[np + 1 + c];
+    return GZ_OK;
+}
+
 gz_status gz_autotune(const gz_plan* p, const gz_graph* g, int use_orientation, void* stream,
                       int* block_warps, int* chunk, int64_t* split_min, int64_t* split_chunk) {
     GZ_RANGE("gz_autotune");

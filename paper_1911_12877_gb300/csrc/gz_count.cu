@@ -64,6 +64,8 @@ struct KQ {
     int32_t hash_log2;     // its slot count is 1 << hash_log2 (0: none)
     int64_t split_min;     // loop-2 candidates from which a unit goes to the split pass
     int64_t split_chunk;   // loop-2 candidates per split-pass work item
+    int32_t merge_pos;     // merged launches: this plan's position in its group
+    uint64_t shared_mask;  // merged launches: the shared loop-1 operations this plan reads
 };
 
 constexpr int kGlobalHashLog2 = 17;  // largest per-warp hash table in scratch (slots)
@@ -107,6 +109,7 @@ struct Deferred {
     int64_t unit;   // launch-space unit index
     int64_t n2;     // loop-2 candidates
     int64_t chunk;  // candidates per split-pass work item
+    int64_t plan;   // merged launches: the plan's position in its group
 };
 
 struct DeferCtl {
@@ -606,7 +609,7 @@ __device__ void process_unit(const KQ& q, int64_t unit, WarpState& ws, int32_t* 
         if (lane == 0) slot = atomicAdd(df->count, 1ull);
         slot = __shfl_sync(kFull, slot, 0);
         if ((int64_t)slot < df->cap) {
-            if (lane == 0) df->list[slot] = Deferred{u, c2.n, q.split_chunk};
+            if (lane == 0) df->list[slot] = Deferred{u, c2.n, q.split_chunk, q.merge_pos};
             __syncwarp();
             return;
         }
@@ -860,6 +863,112 @@ __global__ void __launch_bounds__(256, 2) k_enumerate_split_one(const __grid_con
     if (lane == 0 && s) atomicAdd(count, s);
 }
 
+// Merged program: several plans over one unit space (GzMerged). One warp per
+// unit binds (e0, e1), runs the shared loop-1 operations (mq) once, then each
+// plan's own loops (pq[p]). Per-plan counts gather in the warp's counters in
+// its scratch (cnt_off words in) and are added to counts[] once at the end. A
+// plan's heavy unit is deferred with its position in the group; the split pass
+// then runs only the shared operations that plan reads (its mask).
+__device__ __forceinline__ void bind_shared(const KQ& m, int64_t unit, uint64_t mask, WarpState& ws,
+                                            int32_t* my, int lane, int* status) {
+    const int32_t e0 = m.usrc[unit];
+    ws.emb[0] = e0;
+    ws.emb[1] = m.ucol[unit];
+    ws.itp[1] = unit - m.urp[e0];
+    unsigned long long none = 0;  // the shared operations write buffers, they count nothing
+    const GzProg& P = m.prog;
+    for (int i = P.level_begin[1]; i < P.level_end[1]; ++i)
+        if ((mask >> i) & 1ull) exec_op(m, P.ops[i], ws, my, lane, none, status);
+}
+
+__global__ void __launch_bounds__(256, 2) k_enumerate_merged(const KQ* __restrict__ mq,
+                                                          const KQ* __restrict__ pq, int np,
+                                                          int64_t total_units, int chunk,
+                                                          unsigned long long* __restrict__ work,
+                                                          unsigned long long* __restrict__ counts,
+                                                          int* __restrict__ status,
+                                                          int32_t* __restrict__ scratch,
+                                                          int64_t words_per_warp, int64_t cnt_off,
+                                                          DeferCtl df) {
+    extern __shared__ int32_t smem[];
+    const int lane = threadIdx.x & 31;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int32_t* my = scratch + gwarp * words_per_warp;
+    unsigned long long* wc = reinterpret_cast<unsigned long long*>(my + cnt_off);
+    int32_t* sm = smem + (threadIdx.x >> 5) * kWarpSmemWords;
+    for (int p = lane; p < np; p += 32) wc[p] = 0;
+    __syncwarp();
+    const KQ& m = mq[0];
+    WarpState ws;
+    for (;;) {
+        unsigned long long start = 0;
+        if (lane == 0) start = atomicAdd(work, (unsigned long long)chunk);
+        start = __shfl_sync(kFull, start, 0);
+        if ((int64_t)start >= total_units) break;
+        int64_t end = (int64_t)start + chunk;
+        if (end > total_units) end = total_units;
+        for (int64_t u = (int64_t)start; u < end; ++u) {
+            const int64_t unit = m.unit_lo + u;
+            bind_shared(m, unit, m.shared_mask, ws, my, lane, status);
+            for (int p = 0; p < np; ++p) {
+                unsigned long long acc = 0;
+                process_unit(pq[p], unit, ws, my, sm, lane, acc, status, 0, -1, &df, u);
+                if (__any_sync(kFull, acc != 0)) {
+                    const unsigned long long t = warp_sum(acc);
+                    if (lane == 0) wc[p] += t;
+                }
+            }
+        }
+    }
+    __syncwarp();
+    if (lane == 0)
+        for (int p = 0; p < np; ++p)
+            if (wc[p]) atomicAdd(&counts[pq[p].out_slot], wc[p]);
+}
+
+// Second pass of a merged launch: chunk t of the deferred (unit, plan) records.
+__global__ void __launch_bounds__(256, 2) k_enumerate_merged_split(const KQ* __restrict__ mq,
+                                                                const KQ* __restrict__ pq,
+                                                                const Deferred* __restrict__ dl,
+                                                                const unsigned long long* __restrict__ dcount,
+                                                                int64_t cap,
+                                                                const int64_t* __restrict__ prefix,
+                                                                unsigned long long* __restrict__ work,
+                                                                unsigned long long* __restrict__ counts,
+                                                                int* __restrict__ status,
+                                                                int32_t* __restrict__ scratch,
+                                                                int64_t words_per_warp) {
+    extern __shared__ int32_t smem[];
+    const int lane = threadIdx.x & 31;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int32_t* my = scratch + gwarp * words_per_warp;
+    int32_t* sm = smem + (threadIdx.x >> 5) * kWarpSmemWords;
+    const int64_t n = (int64_t)*dcount < cap ? (int64_t)*dcount : cap;
+    const int64_t total = prefix[n];
+    const KQ& m = mq[0];
+    WarpState ws;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(work, 1ull);
+        t = __shfl_sync(kFull, t, 0);
+        if ((int64_t)t >= total) break;
+        int64_t lo = 0, hi = n - 1;  // last record with prefix <= t
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= (int64_t)t) lo = mid; else hi = mid - 1;
+        }
+        const Deferred rec = dl[lo];
+        const int64_t c0 = ((int64_t)t - prefix[lo]) * rec.chunk;
+        const int64_t unit = m.unit_lo + rec.unit;
+        const KQ& q = pq[rec.plan];
+        bind_shared(m, unit, q.shared_mask, ws, my, lane, status);
+        unsigned long long acc = 0;
+        process_unit(q, unit, ws, my, sm, lane, acc, status, c0, c0 + rec.chunk);
+        const unsigned long long sum = warp_sum(acc);
+        if (lane == 0 && sum) atomicAdd(&counts[q.out_slot], sum);
+    }
+}
+
 void fill_kq(const Query& Q, const LaunchCfg& cfg, KQ& k, uint64_t* words_out) {
     memset(&k, 0, sizeof(KQ));
     k.split_min = Q.split_min > 0 ? Q.split_min : cfg.split_min;
@@ -881,6 +990,7 @@ void fill_kq(const Query& Q, const LaunchCfg& cfg, KQ& k, uint64_t* words_out) {
 // device for each enumeration kernel (8 warps, above the 48 KB default).
 inline size_t cta_smem(int bw) { return (size_t)bw * kWarpSmemWords * 4; }
 std::atomic<unsigned long long> g_attr_enum{0}, g_attr_split{0}, g_attr_one{0}, g_attr_split_one{0};
+std::atomic<unsigned long long> g_attr_merged{0}, g_attr_merged_split{0};
 
 cudaError_t enum_attrs() {
     const int b = (int)cta_smem(8);
@@ -1105,6 +1215,157 @@ gz_status count_launch(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return cuda_fail(e, "enumerate launch");
+    return GZ_OK;
+}
+
+// Scratch layout of a merged launch (per warp): the shared buffers, then the
+// largest own region of any plan (its buffers and, for a fixed-operand last
+// loop, its hash table), then one uint64 counter per plan. Fills the shared
+// descriptor and the plans' buffer offsets when mk / pk are given.
+static uint64_t merged_layout(const GzMerged& m, const gz_graph& g, const GzView& v, KQ* mk, KQ* pk,
+                              uint64_t* cnt_off) {
+    auto cap_of = [&](int dag) { return (uint64_t)(dag ? v.max_out : g.max_deg); };
+    const int ns = m.shared.nbuf;
+    uint64_t off = 0;
+    int64_t soff[GZ_MAXBUF], scap[GZ_MAXBUF];
+    for (int b = 0; b < ns; ++b) {
+        const uint64_t cap = cap_of(m.shared.buf_dag[b]);
+        soff[b] = (int64_t)off;
+        scap[b] = (int64_t)cap;
+        if (mk) { mk->buf_off[b] = soff[b]; mk->buf_cap[b] = scap[b]; }
+        off += (cap + 31) & ~31ull;
+    }
+    const uint64_t shared_words = off;
+    uint64_t own_max = 0;
+    for (size_t i = 0; i < m.progs.size(); ++i) {
+        const GzProg& q = m.progs[i];
+        KQ* k = pk ? pk + i : nullptr;
+        uint64_t po = shared_words;
+        for (int b = 0; b < q.nbuf; ++b) {
+            if (b < ns) {
+                if (k) { k->buf_off[b] = soff[b]; k->buf_cap[b] = scap[b]; }
+                continue;
+            }
+            const uint64_t cap = cap_of(q.buf_dag[b]);
+            if (k) { k->buf_off[b] = (int64_t)po; k->buf_cap[b] = (int64_t)cap; }
+            po += (cap + 31) & ~31ull;
+        }
+        int lg = 0;
+        const uint64_t capmax = (uint64_t)g.max_deg;
+        if (q.flat == 1 && capmax > (uint64_t)kStageWords)
+            while ((1ull << lg) < 2 * capmax && lg < kGlobalHashLog2) ++lg;
+        if (k) {
+            k->hash_off = (int64_t)po;
+            k->hash_log2 = lg;
+        }
+        if (lg) po += 1ull << lg;
+        own_max = std::max(own_max, po - shared_words);
+    }
+    const uint64_t co = (shared_words + own_max + 1) & ~1ull;  // uint64 counters, 8-byte aligned
+    if (cnt_off) *cnt_off = co;
+    return (co + 2 * m.progs.size() + 1) & ~1ull;  // even: every warp's region 8-byte aligned
+}
+
+// The shared operations plan q reads: those writing the buffers its operations
+// and candidate lists use, closed over the shared operations' own inputs.
+static uint64_t shared_mask_of(const GzProg& sh, const GzProg& q) {
+    const int ns = sh.nbuf;
+    uint64_t need = 0;  // bit b: shared buffer b is read
+    for (int i = 0; i < q.nops; ++i)
+        if (q.ops[i].left_buf >= 0 && q.ops[i].left_buf < ns) need |= 1ull << q.ops[i].left_buf;
+    for (int d = 0; d < GZ_MAX_K; ++d)
+        if (q.cand_buf[d] >= 0 && q.cand_buf[d] < ns) need |= 1ull << q.cand_buf[d];
+    uint64_t mask = 0;
+    for (int i = sh.nops - 1; i >= 0; --i)  // writers come before readers
+        if ((need >> sh.ops[i].dst) & 1ull) {
+            mask |= 1ull << i;
+            if (sh.ops[i].left_buf >= 0) need |= 1ull << sh.ops[i].left_buf;
+        }
+    return mask;
+}
+
+uint64_t merged_scratch_words(const GzMerged& m, const gz_graph& g, const GzView& v) {
+    return merged_layout(m, g, v, nullptr, nullptr, nullptr);
+}
+
+uint64_t merged_meta_bytes(const GzMerged& m, int64_t units) {
+    bool split = false;
+    for (const GzProg& q : m.progs) split = split || q.k >= 4;
+    const int64_t cap = split ? defer_cap(units) : 0;
+    return align256(sizeof(KQ) * (m.progs.size() + 1)) + 256 + align256(sizeof(Deferred) * cap) +
+           align256(sizeof(int64_t) * (cap + 1));
+}
+
+gz_status count_merged(const GzMerged& m, const gz_graph* g, const GzView* v, const LaunchCfg& cfg,
+                       cudaStream_t s, unsigned long long* d_counts, int* d_status, void* scratch,
+                       uint64_t scratch_bytes, void* meta, uint64_t meta_bytes) {
+    const int np = (int)m.progs.size();
+    if (np == 0) return GZ_OK;
+    const int64_t units = m.unit_dag ? v->dag_nnz : g->nnz;
+    if (units <= 0) return GZ_OK;
+    std::vector<KQ> h(np + 1);
+    for (int i = 0; i <= np; ++i) {
+        KQ& k = h[i];
+        memset(&k, 0, sizeof(KQ));
+        k.prog = i == 0 ? m.shared : m.progs[i - 1];
+        k.rp = v->rp; k.col = v->col; k.drp = v->dag_rp; k.dcol = v->dag_col;
+        if (m.unit_dag) { k.usrc = v->dag_src; k.ucol = v->dag_col; k.urp = v->dag_rp; }
+        else { k.usrc = v->src; k.ucol = v->col; k.urp = v->rp; }
+        k.unit_lo = 0;
+        k.unit_count = units;
+        k.split_min = cfg.split_min;
+        k.split_chunk = cfg.split_chunk > 0 ? cfg.split_chunk : 1;
+        k.out_slot = i == 0 ? 0 : m.plan_index[i - 1];
+        k.merge_pos = i == 0 ? 0 : i - 1;
+        k.shared_mask = i == 0 ? (m.shared.nops >= 64 ? ~0ull : (1ull << m.shared.nops) - 1)
+                               : shared_mask_of(m.shared, m.progs[i - 1]);
+    }
+    uint64_t cnt_off = 0;
+    const uint64_t words = merged_layout(m, *g, *v, &h[0], h.data() + 1, &cnt_off);
+    const int warps = resident_warps(cfg);
+    if ((uint64_t)warps * words * sizeof(int32_t) > scratch_bytes) {
+        set_error("merged count: scratch too small (%llu bytes needed)",
+                  (unsigned long long)((uint64_t)warps * words * 4));
+        return GZ_ENOMEM;
+    }
+    if (meta_bytes < merged_meta_bytes(m, units)) {
+        set_error("merged count: launch metadata region too small");
+        return GZ_ENOMEM;
+    }
+    bool split = false;
+    for (const GzProg& q : m.progs) split = split || q.k >= 4;
+    const int64_t cap = split ? defer_cap(units) : 0;
+    char* base = reinterpret_cast<char*>(meta);
+    const uint64_t qbytes = align256(sizeof(KQ) * (np + 1));
+    KQ* d = reinterpret_cast<KQ*>(base);
+    unsigned long long* work = reinterpret_cast<unsigned long long*>(base + qbytes);
+    Deferred* dl = reinterpret_cast<Deferred*>(base + qbytes + 256);
+    int64_t* prefix = reinterpret_cast<int64_t*>(base + qbytes + 256 + align256(sizeof(Deferred) * cap));
+    cudaError_t e = enum_attrs();
+    if (e == cudaSuccess) e = smem_attr_once(k_enumerate_merged, (int)cta_smem(8), g_attr_merged);
+    if (e == cudaSuccess) e = smem_attr_once(k_enumerate_merged_split, (int)cta_smem(8), g_attr_merged_split);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d, h.data(), sizeof(KQ) * (np + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(work, 0, 32, s);
+    if (e == cudaSuccess) {
+        int blocks = warps / cfg.block_warps;
+        if (cfg.grid_frac < 1.0) blocks = std::max(1, (int)(blocks * cfg.grid_frac));
+        DeferCtl df{split ? dl : nullptr, work + 2, cap};
+        // a merged unit carries every plan's work: one unit per queue pop
+        k_enumerate_merged<<<blocks, cfg.block_warps * 32, cta_smem(cfg.block_warps), s>>>(
+            d, d + 1, np, units, 1, work, d_counts, d_status, reinterpret_cast<int32_t*>(scratch),
+            (int64_t)words, (int64_t)cnt_off, df);
+        GZ_COUNT_LAUNCH();
+        if (split) {
+            k_split_scan<<<1, 1024, 0, s>>>(dl, work + 2, cap, prefix);
+            GZ_COUNT_LAUNCH();
+            k_enumerate_merged_split<<<blocks, cfg.block_warps * 32, cta_smem(cfg.block_warps), s>>>(
+                d, d + 1, dl, work + 2, cap, prefix, work + 1, d_counts, d_status,
+                reinterpret_cast<int32_t*>(scratch), (int64_t)words);
+            GZ_COUNT_LAUNCH();
+        }
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "merged launch");
     return GZ_OK;
 }
 

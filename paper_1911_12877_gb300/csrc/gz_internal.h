@@ -212,6 +212,33 @@ uint64_t one_meta_bytes(const Query& Q, bool split);
 gz_status count_one_in_region(const Query& Q, const LaunchCfg& cfg, cudaStream_t s, void* region,
                               uint64_t scratch_bytes, bool split, uint64_t* out_count);
 
+// merged programs (gz_plan.cpp builds them, gz_count.cu runs them): several
+// plans that share a unit space compiled into one mining program (Sec. 3: one
+// program for several patterns). The loop-1 set operations that write buffers
+// are deduplicated across the plans into `shared` (buffers [0, shared.nbuf));
+// each plan's program keeps its other operations, with its own buffers
+// numbered after the shared ones. One warp per unit binds (e0, e1), runs the
+// shared operations once, then each plan's remaining loops.
+struct GzMerged {
+    int unit_dag = 0;
+    GzProg shared;                      // level-1 buffer-writing operations only
+    std::vector<GzProg> progs;          // per plan, rewritten
+    std::vector<const gz_plan*> plans;
+    std::vector<int> plan_index;        // each plan's index in the caller's list (count slot)
+};
+// Groups the plans idx[0..n) by unit space and merges each group (a group is
+// split where the merged program would outgrow the kernel's limits).
+gz_status merge_plans(const gz_plan* const* plans, const int* idx, int n, std::vector<GzMerged>& out);
+// Scratch words per warp and device bytes beside the scratch of one merged launch.
+uint64_t merged_scratch_words(const GzMerged& m, const gz_graph& g, const GzView& v);
+uint64_t merged_meta_bytes(const GzMerged& m, int64_t units);
+// One merged launch (plus its split pass) over all units of view v: plan i of
+// the group adds its count to d_counts[m.plan_index[i]]. scratch must hold
+// resident_warps(cfg) * merged_scratch_words words; meta merged_meta_bytes.
+gz_status count_merged(const GzMerged& m, const gz_graph* g, const GzView* v, const LaunchCfg& cfg,
+                       cudaStream_t s, unsigned long long* d_counts, int* d_status, void* scratch,
+                       uint64_t scratch_bytes, void* meta, uint64_t meta_bytes);
+
 // clique side (gz_clique.cu): oriented k-cliques as bitsets over the root's out-list
 constexpr int kCliqueMaxOut = 1024;   // largest out-list whose rows fit in shared memory
 constexpr int kCliqueWork = 3;        // zeroed work counters a clique query needs

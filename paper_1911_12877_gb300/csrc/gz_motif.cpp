@@ -164,11 +164,7 @@ gz_status gz_count_motifs(const gz_graph* g, int k, int use_orientation, void* s
     gz_motif_patterns(k, adj.data(), np, &np);
     std::vector<gz_plan*> plans(np, nullptr);
     for (int p = 0; p < np && st == GZ_OK; ++p) st = gz_plan_create(k, adj.data() + (size_t)p * k * k, 0, &plans[p]);
-    if (st == GZ_OK) {
-        std::vector<const gz_graph*> gs(np, g);
-        std::vector<int> ori(np, use_orientation);
-        st = gz_count_batch(plans.data(), gs.data(), ori.data(), np, stream, counts);
-    }
+    if (st == GZ_OK) st = gz_count_merged(plans.data(), np, g, use_orientation, stream, counts);
     for (gz_plan* p : plans) gz_plan_destroy(p);
     return st;
 }

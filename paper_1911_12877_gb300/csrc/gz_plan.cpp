@@ -443,3 +443,175 @@ gz_status list_schedules(int k, const uint8_t* adj, int32_t* orders, int cap, in
 }
 
 }  // namespace gz
+
+// ------------------------------------------------------------ merged programs
+
+namespace gz {
+
+namespace {
+
+// Key of a level-1 operation that writes a buffer: every field except the
+// destination, with the left buffer in the merged numbering, and the capacity
+// class of the destination.
+struct OpKey {
+    int8_t v[8 + 3 * GZ_MAXRIGHT + 2];
+    bool operator<(const OpKey& o) const { return memcmp(v, o.v, sizeof(v)) < 0; }
+};
+
+OpKey op_key(const GzOp& op, int left_merged, int dst_dag) {
+    OpKey k;
+    memset(&k, 0, sizeof(k));
+    int i = 0;
+    k.v[i++] = op.level;
+    k.v[i++] = (int8_t)left_merged;
+    k.v[i++] = op.left_pos;
+    k.v[i++] = op.left_dag;
+    k.v[i++] = op.left_iter;
+    k.v[i++] = op.nright;
+    k.v[i++] = op.bound_pos;
+    k.v[i++] = (int8_t)op.excl_mask;
+    for (int r = 0; r < GZ_MAXRIGHT; ++r) {
+        k.v[i++] = r < op.nright ? op.right_pos[r] : 0;
+        k.v[i++] = r < op.nright ? op.right_sub[r] : 0;
+        k.v[i++] = r < op.nright ? op.right_dag[r] : 0;
+    }
+    k.v[i++] = (int8_t)dst_dag;
+    return k;
+}
+
+// One group under construction.
+struct MergeState {
+    GzMerged m;
+    std::map<OpKey, int> shared;  // key -> merged buffer
+};
+
+// Tries to add plan p to the group: its level-1 buffer-writing operations are
+// matched against the group's or added to them, and its program is rewritten
+// without them. Returns false (the group unchanged) when the merged program
+// would outgrow the kernel's operation or buffer limits.
+bool add_to_group(MergeState& st, const gz_plan* p, int caller_index) {
+    const GzProg& src = p->prog;
+    MergeState trial = st;  // committed only on success
+    GzProg& sh = trial.m.shared;
+    std::vector<int> map(src.nbuf, -1);  // plan buffer -> shared buffer
+    for (int i = src.level_begin[1]; i < src.level_end[1]; ++i) {
+        const GzOp& op = src.ops[i];
+        if (op.dst < 0) continue;
+        const int left = op.left_buf >= 0 ? map[op.left_buf] : -1;
+        if (op.left_buf >= 0 && left < 0) return false;  // reads a buffer no shared op writes
+        const OpKey key = op_key(op, left, src.buf_dag[op.dst]);
+        auto it = trial.shared.find(key);
+        if (it != trial.shared.end()) {
+            map[op.dst] = it->second;
+            continue;
+        }
+        if (sh.nops >= GZ_MAXOPS || sh.nbuf >= GZ_MAXBUF) return false;
+        const int b = sh.nbuf++;
+        sh.buf_dag[b] = src.buf_dag[op.dst];
+        GzOp m = op;
+        m.dst = (int8_t)b;
+        m.left_buf = (int8_t)left;
+        sh.ops[sh.nops++] = m;
+        trial.shared[key] = b;
+        map[op.dst] = b;
+    }
+    // the plan's own buffers keep a provisional numbering, -(2 + own index),
+    // until the group is complete (then they follow the shared ones)
+    GzProg q;
+    memset(&q, 0, sizeof(q));
+    q.k = src.k;
+    q.unit_dag = src.unit_dag;
+    q.flat = src.flat;
+    int own = 0;
+    std::vector<int> own_index(src.nbuf, -1);
+    for (int b = 0; b < src.nbuf; ++b)
+        if (map[b] < 0) own_index[b] = own++;
+    auto remap = [&](int b) -> int { return b < 0 ? b : (map[b] >= 0 ? map[b] : -(2 + own_index[b])); };
+    for (int t = 0; t < GZ_MAX_K; ++t) {
+        q.level_begin[t] = (int8_t)q.nops;
+        if (t < src.k)
+            for (int i = src.level_begin[t]; i < src.level_end[t]; ++i) {
+                const GzOp& op = src.ops[i];
+                if (t == 1 && op.dst >= 0) continue;  // computed by the shared operations
+                GzOp o = op;
+                o.dst = (int8_t)remap(op.dst);
+                o.left_buf = (int8_t)remap(op.left_buf);
+                q.ops[q.nops++] = o;
+            }
+        q.level_end[t] = (int8_t)q.nops;
+    }
+    for (int d = 0; d < GZ_MAX_K; ++d) {
+        q.cand_buf[d] = (int8_t)remap(src.cand_buf[d]);
+        q.cand_pos[d] = src.cand_pos[d];
+        q.cand_bound[d] = src.cand_bound[d];
+        q.cand_dag[d] = src.cand_dag[d];
+        q.cand_excl[d] = src.cand_excl[d];
+    }
+    q.nbuf = own;  // own buffers only, until the group is finished
+    for (int b = 0; b < src.nbuf; ++b)
+        if (own_index[b] >= 0) q.buf_dag[own_index[b]] = src.buf_dag[b];
+    int own_max = own;
+    for (const GzProg& o : trial.m.progs) own_max = std::max(own_max, o.nbuf);
+    if (sh.nbuf + own_max > GZ_MAXBUF) return false;
+    trial.m.progs.push_back(q);
+    trial.m.plans.push_back(p);
+    trial.m.plan_index.push_back(caller_index);
+    st = std::move(trial);
+    return true;
+}
+
+// Final numbering: each plan's own buffers after the group's shared ones.
+void finish_group(GzMerged& m) {
+    const int ns = m.shared.nbuf;
+    m.shared.k = 2;
+    m.shared.unit_dag = m.unit_dag;
+    for (int t = 0; t < GZ_MAX_K; ++t) {
+        m.shared.level_begin[t] = t <= 1 ? 0 : (int8_t)m.shared.nops;
+        m.shared.level_end[t] = t == 1 ? (int8_t)m.shared.nops : m.shared.level_begin[t];
+    }
+    for (GzProg& q : m.progs) {
+        auto fin = [&](int8_t b) -> int8_t { return b <= -2 ? (int8_t)(ns + (-b - 2)) : b; };
+        for (int i = 0; i < q.nops; ++i) {
+            q.ops[i].dst = fin(q.ops[i].dst);
+            q.ops[i].left_buf = fin(q.ops[i].left_buf);
+        }
+        for (int d = 0; d < GZ_MAX_K; ++d) q.cand_buf[d] = fin(q.cand_buf[d]);
+        int8_t dag[GZ_MAXBUF] = {};
+        for (int b = 0; b < ns; ++b) dag[b] = m.shared.buf_dag[b];
+        for (int b = 0; b < q.nbuf; ++b) dag[ns + b] = q.buf_dag[b];
+        q.nbuf += ns;
+        memcpy(q.buf_dag, dag, sizeof(dag));
+    }
+}
+
+}  // namespace
+
+gz_status merge_plans(const gz_plan* const* plans, const int* idx, int n, std::vector<GzMerged>& out) {
+    out.clear();
+    for (int dag = 0; dag <= 1; ++dag) {
+        std::vector<MergeState> groups;
+        for (int i = 0; i < n; ++i) {
+            const gz_plan* p = plans[idx[i]];
+            if (p->prog.unit_dag != dag) continue;
+            bool placed = false;
+            for (MergeState& g : groups)
+                if (add_to_group(g, p, idx[i])) { placed = true; break; }
+            if (!placed) {
+                groups.emplace_back();
+                memset(&groups.back().m.shared, 0, sizeof(GzProg));
+                groups.back().m.unit_dag = dag;
+                if (!add_to_group(groups.back(), p, idx[i])) {
+                    set_error("merge: a plan does not fit the merged program's limits");
+                    return GZ_EOVERFLOW;
+                }
+            }
+        }
+        for (MergeState& g : groups) {
+            finish_group(g.m);
+            out.push_back(std::move(g.m));
+        }
+    }
+    return GZ_OK;
+}
+
+}  // namespace gz
