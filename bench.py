@@ -530,9 +530,11 @@ def run_patterns(args, dist, world, rank, local):
 
     Per pattern: the oracle's sampled root ranges (hub blocks to low-degree
     blocks) are counted and timed, each count checked against the stored oracle
-    value, and E over those ranges / their count time gives the throughput. The
-    full count is timed for the patterns in --full (its cost on this graph is
-    listed in the design notes for the others)."""
+    value, and E over those ranges / their count time gives the throughput (one
+    range per call). batched_ranges times the same ranges of all patterns in one
+    gz_count_batch_ranges call. The full count is timed for the patterns in
+    --full (its cost on this graph is listed in the design notes for the
+    others)."""
     import torch
     import paper_1911_12877_gb300 as gz
     import synthetic as S
@@ -578,12 +580,69 @@ def run_patterns(args, dist, world, rank, local):
         res[name] = r
     launches = gz.kernel_launches() - l0
     value = tot_e / (tot_ms / 1e3) if tot_ms > 0 else None
+    extra = {}
+    if gold:
+        # the same sampled ranges, all patterns at once: one gz_count_batch_ranges
+        # call (a few roots per range leave most of the device idle when each
+        # range is counted alone)
+        plans, ranges, wants, e_b = [], [], [], 0
+        for name in names:
+            if name not in gold["patterns"]:
+                continue
+            p = gz.Plan(name)
+            for lo, hi, want, e in gold["patterns"][name]["samples"]:
+                plans.append(p)
+                ranges.append((lo, hi))
+                wants.append(want)
+                e_b += e
+        nb = len(plans)
+        l1 = gz.kernel_launches()
+        got, ms = _time_counts(lambda: gz.count_batch_ranges(plans, [G] * nb, [True] * nb, ranges),
+                               args.steps, stream)
+        if got != wants:
+            bad = [(ranges[i], got[i], wants[i]) for i in range(nb) if got[i] != wants[i]]
+            raise SystemExit(f"batched ranges differ from the oracle: {bad[:3]}")
+        med = statistics.median(ms)
+        extra["batched_ranges"] = {
+            "queries": nb, "elems": e_b, **_summary(ms), "elems_per_s": e_b / (med / 1e3),
+            "hbm_frac_algorithmic": round(4 * e_b / (med / 1e3) / 1e9 / peak, 4),
+            "speedup_vs_one_range_per_call": round(tot_ms / med, 3) if med > 0 else None,
+            "gpu_launches_per_call": (gz.kernel_launches() - l1) // (args.steps + 1),
+            "oracle_parity": "ok"}
     return _line("intersected elements/s over the oracle's sampled root ranges", value, UNIT, args,
                  world, tot_ms,
                  {"workload": f"c4, diamond, paw, house, chordal5 with restrictions + orientation, "
                               f"R-MAT scale {scale} ef 16 seed {scale}", "n": g.n, "nnz": g.nnz,
                   "l2": "graph larger than L2; not flushed between ranges"},
-                 patterns=res, orient_ms=_summary(t_or), gpu_launches=launches)
+                 patterns=res, orient_ms=_summary(t_or), gpu_launches=launches, **extra)
+
+
+def run_pattern_samples(args, dist, world, rank, local):
+    """One count per pattern on the oracle's heaviest sampled root range of R-MAT
+    scale 22 (the range with the most list elements E), each checked against the
+    oracle's value: a short fixed launch sequence for profiling the general
+    kernel (one k_enumerate_one launch per pattern, plus its split pass)."""
+    import torch
+    import paper_1911_12877_gb300 as gz
+    import synthetic as S
+    from synthetic.patterns import PATTERN_SET
+    torch.cuda.set_device(local)
+    g = S.rmat(22, 16, 22)
+    gold = load_golden("patterns_rmat22.json")
+    G = gz.Graph.from_csr(g).orient()
+    names = args.patterns.split(",") if args.patterns else PATTERN_SET
+    out = {}
+    t0 = time.perf_counter()
+    for name in names:
+        lo, hi, want, e = max(gold["patterns"][name]["samples"], key=lambda x: x[3])
+        got = gz.count(gz.Plan(name), G, True, lo, hi)
+        if got != want:
+            raise SystemExit(f"{name} roots [{lo},{hi}): {got} != oracle {want}")
+        out[name] = {"roots": [lo, hi], "count": got, "elems": e}
+    ms = 1e3 * (time.perf_counter() - t0)
+    return _line("one count per pattern on its heaviest oracle sample", ms, "ms", args, world, ms,
+                 {"workload": f"{names} on R-MAT scale 22 ef 16 seed 22 (oriented)"}, hib=False,
+                 samples=out, oracle_parity="ok")
 
 
 def run_batched(args, dist, world, rank, local):
@@ -939,7 +998,8 @@ def run_planner(args, dist, world, rank, local):
                                "patterns under 30 ms each; K7 minus one edge 0.6 ms (2x8 Xeon cores)")
 
 
-EXTRA = {"triangle": run_triangle, "patterns": run_patterns, "batched": run_batched,
+EXTRA = {"triangle": run_triangle, "patterns": run_patterns, "pattern_samples": run_pattern_samples,
+         "batched": run_batched,
          "served": run_served, "motifs": run_motifs, "schedules": run_schedules,
          "planner": run_planner}
 
@@ -951,8 +1011,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gz", choices=["gz", "reference"])
     ap.add_argument("--config", default="clique",
-                    choices=["clique", "triangle", "patterns", "batched", "served", "motifs",
-                             "schedules", "planner"])
+                    choices=["clique", "triangle", "patterns", "pattern_samples", "batched", "served",
+                             "motifs", "schedules", "planner"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-subconfigs", action="store_true",

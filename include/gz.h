@@ -288,6 +288,19 @@ gz_status gz_count_batch(const gz_plan* const* plans, const gz_graph* const* gra
                          uint64_t* out_counts);
 
 /*
+ * gz_count_batch over root ranges: query i counts only the instances whose root
+ * (first scheduled vertex) lies in [root_lo[i], root_hi[i]), as gz_count_ex
+ * does (root_lo < 0 is 0; root_hi < 0 or > n is n; an empty range counts 0).
+ * The ranges of one (plan, graph) partition its count, so disjoint ranges of a
+ * heavy query spread over one launch. root_lo and root_hi are host arrays of nq
+ * entries. Errors: as gz_count_batch; GZ_EINVAL for NULL range arrays.
+ */
+gz_status gz_count_batch_ranges(const gz_plan* const* plans, const gz_graph* const* graphs,
+                                const int* use_orientation, const int64_t* root_lo,
+                                const int64_t* root_hi, int nq, void* stream,
+                                uint64_t* out_counts);
+
+/*
  * Autotuner (no paper counterpart): times candidate launch settings of the
  * general kernel for this (plan, graph, view) with CUDA events on `stream`
  * (median of 3 runs each) and keeps the fastest; later gz_count and

@@ -27,7 +27,7 @@ EXPORTS = [
     "gz_load_csr", "gz_orient", "gz_graph_info", "gz_graph_export", "gz_graph_destroy",
     "gz_pattern_named", "gz_plan_create", "gz_plan_create_with_order", "gz_plan_info",
     "gz_plan_schedules", "gz_plan_describe", "gz_plan_destroy", "gz_count", "gz_count_ex", "gz_scratch_bytes",
-    "gz_count_batch", "gz_count_noalloc", "gz_autotune", "gz_server_create", "gz_server_submit", "gz_server_wait",
+    "gz_count_batch", "gz_count_batch_ranges", "gz_count_noalloc", "gz_autotune", "gz_server_create", "gz_server_submit", "gz_server_wait",
     "gz_server_replay", "gz_server_destroy", "gz_last_error", "gz_version", "gz_kernel_launches",
     "gz_allocations", "gz_count_merged",
     "gz_motif_patterns", "gz_count_motifs", "gz_plan_create_measured", "gz_schedule_times",
@@ -98,6 +98,8 @@ def lib() -> ctypes.CDLL:
         "gz_scratch_bytes": [_P, _P, I, _u64p],
         "gz_count_noalloc": [_P, _P, I, _P, _u64p],
         "gz_count_batch": [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(I), I, _P, _u64p],
+        "gz_count_batch_ranges": [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(I), _i64p, _i64p, I, _P,
+                                  _u64p],
         "gz_count_merged": [ctypes.POINTER(_P), I, _P, I, _P, _u64p],
         "gz_autotune": [_P, _P, I, _P, ctypes.POINTER(I), ctypes.POINTER(I), _i64p, _i64p],
         "gz_motif_patterns": [I, _u8p, I, ctypes.POINTER(I)],
@@ -374,6 +376,19 @@ def count_batch(plans, graphs, orientation, stream=None) -> list[int]:
     O = (ctypes.c_int * nq)(*[int(o) for o in orientation])
     out = (ctypes.c_uint64 * nq)()
     _check(lib().gz_count_batch(P, G, O, nq, _stream(stream), out), "gz_count_batch")
+    return list(out)
+
+
+def count_batch_ranges(plans, graphs, orientation, ranges, stream=None) -> list[int]:
+    """gz_count_batch_ranges: query i counts the roots in ranges[i] = (lo, hi)."""
+    nq = len(plans)
+    P = (_P * nq)(*[p.handle for p in plans])
+    G = (_P * nq)(*[g.handle for g in graphs])
+    O = (ctypes.c_int * nq)(*[int(o) for o in orientation])
+    lo = (ctypes.c_int64 * nq)(*[int(r[0]) for r in ranges])
+    hi = (ctypes.c_int64 * nq)(*[int(r[1]) for r in ranges])
+    out = (ctypes.c_uint64 * nq)()
+    _check(lib().gz_count_batch_ranges(P, G, O, lo, hi, nq, _stream(stream), out), "gz_count_batch_ranges")
     return list(out)
 
 

@@ -50,6 +50,7 @@ struct Arena {
     void* ptr = nullptr;
     uint64_t bytes = 0;
     int device = -1;
+    unsigned long long* pinned = nullptr;  // 16 bytes of page-locked memory for count read-backs
 };
 Arena& arena() {
     static Arena a;
@@ -335,7 +336,11 @@ gz_status run_queries(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream_
         const uint64_t scr = (uint64_t)resident_warps(cfg) * scratch_words_per_warp(*q.prog, *q.g, *q.view) * 4;
         gz_status st = arena_reserve(a, meta + scr);
         if (st != GZ_OK) return st;
-        return count_one_in_region(q, cfg, s, a.ptr, a.bytes - meta, true, out_counts);
+        if (!a.pinned && gz_malloc_host(&a.pinned, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            a.pinned = nullptr;  // fall back to a pageable read-back
+        }
+        return count_one_in_region(q, cfg, s, a.ptr, a.bytes - meta, true, out_counts, a.pinned);
     }
     // arena: counts [nq], status, clique work counters [kCliqueWork nq] | launch metadata | scratch
     const size_t hwords = (size_t)nq + 1 + kCliqueWork * (size_t)nq;
@@ -741,20 +746,20 @@ gz_status gz_scratch_bytes(const gz_plan* p, const gz_graph* g, int use_orientat
     return GZ_OK;
 }
 
-gz_status gz_count_batch(const gz_plan* const* plans, const gz_graph* const* graphs,
-                         const int* use_orientation, int nq, void* stream, uint64_t* out_counts) {
-    GZ_RANGE("gz_count_batch");
+static gz_status count_batch(const char* who, const gz_plan* const* plans, const gz_graph* const* graphs,
+                             const int* use_orientation, const int64_t* root_lo, const int64_t* root_hi,
+                             int nq, void* stream, uint64_t* out_counts) {
     if (nq < 0 || (nq > 0 && (!plans || !graphs || !out_counts))) {
-        set_error("gz_count_batch: bad arguments");
+        set_error("%s: bad arguments", who);
         return GZ_EINVAL;
     }
     if (nq == 0) return GZ_OK;
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<Query> qs(nq);
     for (int i = 0; i < nq; ++i) {
-        if (!plans[i] || !graphs[i]) { set_error("gz_count_batch: NULL plan or graph at %d", i); return GZ_EINVAL; }
+        if (!plans[i] || !graphs[i]) { set_error("%s: NULL plan or graph at %d", who, i); return GZ_EINVAL; }
         gz_status st = prepare_query(plans[i], graphs[i], use_orientation ? use_orientation[i] : 0,
-                                     0, -1, s, qs[i]);
+                                     root_lo ? root_lo[i] : 0, root_hi ? root_hi[i] : -1, s, qs[i]);
         if (st != GZ_OK) return st;
     }
     // heaviest queries first (largest unit count x depth), so their tails start early
@@ -788,6 +793,25 @@ gz_status gz_count_batch(const gz_plan* const* plans, const gz_graph* const* gra
     if (st != GZ_OK) return st;
     for (int i = 0; i < nq; ++i) out_counts[idx[i]] = res[i];
     return GZ_OK;
+}
+
+gz_status gz_count_batch(const gz_plan* const* plans, const gz_graph* const* graphs,
+                         const int* use_orientation, int nq, void* stream, uint64_t* out_counts) {
+    GZ_RANGE("gz_count_batch");
+    return count_batch("gz_count_batch", plans, graphs, use_orientation, nullptr, nullptr, nq, stream,
+                       out_counts);
+}
+
+gz_status gz_count_batch_ranges(const gz_plan* const* plans, const gz_graph* const* graphs,
+                                const int* use_orientation, const int64_t* root_lo,
+                                const int64_t* root_hi, int nq, void* stream, uint64_t* out_counts) {
+    GZ_RANGE("gz_count_batch_ranges");
+    if (nq > 0 && (!root_lo || !root_hi)) {
+        set_error("gz_count_batch_ranges: NULL root range arrays");
+        return GZ_EINVAL;
+    }
+    return count_batch("gz_count_batch_ranges", plans, graphs, use_orientation, root_lo, root_hi, nq, stream,
+                       out_counts);
 }
 
 gz_status gz_count_merged(const gz_plan* const* plans, int np, const gz_graph* g, int use_orientation,

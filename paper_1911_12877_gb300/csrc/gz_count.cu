@@ -659,7 +659,7 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 }
 
 // Persistent enumeration kernel over a batch of queries (nq >= 1).
-__global__ void __launch_bounds__(256, 2) k_enumerate(const KQ* __restrict__ qs, int nq,
+__global__ void __launch_bounds__(256, 3) k_enumerate(const KQ* __restrict__ qs, int nq,
                                                    int64_t total_units, int chunk,
                                                    unsigned long long* __restrict__ work,
                                                    unsigned long long* __restrict__ counts,
@@ -736,7 +736,7 @@ __global__ void __launch_bounds__(1024) k_split_scan(const Deferred* __restrict_
 }
 
 // Second pass: chunk t of the deferred units, one per warp pop.
-__global__ void __launch_bounds__(256, 2) k_enumerate_split(const KQ* __restrict__ qs, int nq,
+__global__ void __launch_bounds__(256, 3) k_enumerate_split(const KQ* __restrict__ qs, int nq,
                                                          const Deferred* __restrict__ dl,
                                                          const unsigned long long* __restrict__ dcount,
                                                          int64_t cap,
@@ -797,7 +797,7 @@ __global__ void __launch_bounds__(256, 2) k_enumerate_split(const KQ* __restrict
 // status, deferred records, per-warp scratch) lives in one region the caller
 // provides, so a count allocates nothing. With df.list set, heavy units are
 // recorded for k_enumerate_split_one as in k_enumerate.
-__global__ void __launch_bounds__(256, 2) k_enumerate_one(const __grid_constant__ KQ q,
+__global__ void __launch_bounds__(256, 3) k_enumerate_one(const __grid_constant__ KQ q,
                                                        int64_t total_units, int chunk,
                                                        unsigned long long* __restrict__ work,
                                                        unsigned long long* __restrict__ count,
@@ -826,7 +826,7 @@ __global__ void __launch_bounds__(256, 2) k_enumerate_one(const __grid_constant_
 }
 
 // Second pass of k_enumerate_one: chunk t of the deferred units, one per warp pop.
-__global__ void __launch_bounds__(256, 2) k_enumerate_split_one(const __grid_constant__ KQ q,
+__global__ void __launch_bounds__(256, 3) k_enumerate_split_one(const __grid_constant__ KQ q,
                                                              const Deferred* __restrict__ dl,
                                                              const unsigned long long* __restrict__ dcount,
                                                              int64_t cap,
@@ -881,7 +881,7 @@ __device__ __forceinline__ void bind_shared(const KQ& m, int64_t unit, uint64_t 
         if ((mask >> i) & 1ull) exec_op(m, P.ops[i], ws, my, lane, none, status);
 }
 
-__global__ void __launch_bounds__(256, 2) k_enumerate_merged(const KQ* __restrict__ mq,
+__global__ void __launch_bounds__(256, 3) k_enumerate_merged(const KQ* __restrict__ mq,
                                                           const KQ* __restrict__ pq, int np,
                                                           int64_t total_units, int chunk,
                                                           unsigned long long* __restrict__ work,
@@ -927,7 +927,7 @@ __global__ void __launch_bounds__(256, 2) k_enumerate_merged(const KQ* __restric
 }
 
 // Second pass of a merged launch: chunk t of the deferred (unit, plan) records.
-__global__ void __launch_bounds__(256, 2) k_enumerate_merged_split(const KQ* __restrict__ mq,
+__global__ void __launch_bounds__(256, 3) k_enumerate_merged_split(const KQ* __restrict__ mq,
                                                                 const KQ* __restrict__ pq,
                                                                 const Deferred* __restrict__ dl,
                                                                 const unsigned long long* __restrict__ dcount,
@@ -1058,9 +1058,11 @@ uint64_t one_meta_bytes(const Query& Q, bool split) {
 // pass-2 queue, deferred-record count) and deferred records, then scratch_bytes
 // of per-warp scratch. Launches fewer warps when the scratch would not hold a
 // full grid. Allocates nothing. Synchronous: the count and status are read back
-// into host locals. split = false runs no second pass (every unit in the first).
+// into pinned (16 bytes of page-locked host memory) or, when it is NULL, host
+// locals. split = false runs no second pass (every unit in the first).
 gz_status count_one_in_region(const Query& Q, const LaunchCfg& cfg, cudaStream_t s, void* region,
-                              uint64_t scratch_bytes, bool split, uint64_t* out_count) {
+                              uint64_t scratch_bytes, bool split, uint64_t* out_count,
+                              unsigned long long* pinned) {
     KQ k;
     uint64_t words = 0;
     fill_kq(Q, cfg, k, &words);
@@ -1109,8 +1111,9 @@ gz_status count_one_in_region(const Query& Q, const LaunchCfg& cfg, cudaStream_t
         }
         e = cudaGetLastError();
     }
-    unsigned long long h[2] = {0, 0};
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h, hdr + 1, sizeof(h), cudaMemcpyDeviceToHost, s);
+    unsigned long long local[2] = {0, 0};
+    unsigned long long* h = pinned ? pinned : local;  // pinned: an asynchronous 16-byte read-back
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, hdr + 1, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "count (region)");
     if ((int)h[1] != 0) {

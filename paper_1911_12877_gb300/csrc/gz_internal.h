@@ -210,7 +210,8 @@ constexpr uint64_t kRegionHeader = 256;
 // the deferred records of the second pass).
 uint64_t one_meta_bytes(const Query& Q, bool split);
 gz_status count_one_in_region(const Query& Q, const LaunchCfg& cfg, cudaStream_t s, void* region,
-                              uint64_t scratch_bytes, bool split, uint64_t* out_count);
+                              uint64_t scratch_bytes, bool split, uint64_t* out_count,
+                              unsigned long long* pinned = nullptr);
 
 // merged programs (gz_plan.cpp builds them, gz_count.cu runs them): several
 // plans that share a unit space compiled into one mining program (Sec. 3: one

@@ -332,6 +332,20 @@ def test_clique_rmat20_full_and_sampled():
         assert gz.count(k5, G, True) == gold["k5"]["count"]
 
 
+def test_served_rmat24_sampled():
+    """The served workload's graph (R-MAT 24, ef 16, seed 24): every pattern of the
+    request mix on the oracle's sampled root ranges (reindexed ids)."""
+    gold = json.load(open(os.path.join(GOLDEN, "served_rmat24.json")))
+    g = S.rmat_served()
+    assert gold["nnz"] == g.nnz
+    G = gz.Graph.from_csr(g).orient()
+    for name, rec in gold["patterns"].items():
+        p = gz.Plan(name)
+        assert p.info()["order"] == rec["order"]
+        for lo, hi, want, _ in rec["samples"]:
+            assert gz.count(p, G, True, lo, hi) == want, (name, lo, hi)
+
+
 def test_patterns_rmat22_sampled():
     """Arbitrary-pattern workload (R-MAT scale 22, ef 16, seed 22, oriented):
     sampled root ranges against stored oracle counts."""
@@ -477,6 +491,29 @@ def test_count_merged_against_oracle(oriented):
         got = gz.count_merged(plans, G, orientation=oriented)
         assert got == [gz.count(p, G, oriented) for p in plans]
         assert got == [oracle_count(n, g) for n in names]
+
+
+def test_batch_ranges_against_oracle():
+    """gz_count_batch_ranges: root ranges of general and clique queries on two
+    graphs, oriented and not, in one call (empty, clamped and out-of-range
+    bounds included): each range's count equals the oracle's on that range."""
+    queries = []
+    general = ["triangle", "paw", "c4", "diamond", "k4", "k5"]
+    for g, names in ((S.rmat(12, 16, 41), general), (S.random_small(80, 0.2, 42), general + ["house"])):
+        G = gz.Graph.from_csr(g).orient()
+        n = g.n
+        cuts = [-5, 0, 3, n // 7, n // 2, n // 2, n + 10]
+        for name in names:
+            p = gz.Plan(name)
+            for ori in (True, False):
+                for lo, hi in zip(cuts[:-1], cuts[1:]):
+                    queries.append((p, G, ori, lo, hi, name, g))
+    got = gz.count_batch_ranges([q[0] for q in queries], [q[1] for q in queries],
+                                [q[2] for q in queries], [(q[3], q[4]) for q in queries])
+    for (p, G, ori, lo, hi, name, g), c in zip(queries, got):
+        lo_c, hi_c = max(lo, 0), min(hi, g.n)
+        want = 0 if lo_c >= hi_c else oracle_count(name, g, oriented=ori, lo=lo_c, hi=hi_c)
+        assert c == want, (name, g.name, ori, lo, hi)
 
 
 def test_count_merged_split_pass():
