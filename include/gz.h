@@ -204,7 +204,7 @@ void gz_plan_destroy(gz_plan* p);
  * the exact count. Scratch is allocated by the library and reused.
  *
  * Oriented k-cliques (4 <= k <= 8) run on the bitset clique kernels: the rows of
- * roots with at least 128 out-neighbours are built once per out-list view and
+ * roots with 33 to 1024 out-neighbours are built once per out-list view and
  * kept on the device until the view is rebuilt (gz_orient) or the graph is
  * destroyed; roots with more than 8192 out-neighbours go to the general kernel
  * in the same call. Every other plan runs on the general kernel, whose first
@@ -219,14 +219,19 @@ typedef struct {
     int64_t root_lo, root_hi; /* only roots (first scheduled vertex) in [lo, hi); hi < 0 = n */
     int block_warps;          /* warps per CTA, 0 = default */
     int chunk;                /* work units per queue pop, 0 = default or autotuned */
-    int64_t split_min;        /* loop-2 candidates from which a unit goes to the split pass, 0 = default or autotuned */
-    int64_t split_chunk;      /* loop-2 candidates per split-pass work item, 0 = default or autotuned */
+    int64_t split_min;        /* loop-2 candidates from which a unit goes to the split pass, 0 = autotuned or automatic */
+    int64_t split_chunk;      /* loop-2 candidates per split-pass work item, 0 = autotuned or automatic */
 } gz_count_opts;
 
 /*
  * gz_count with options. Roots are vertex ids in the view being counted
  * (reindexed ids when use_orientation = 1). The sum over a partition of the
- * root range equals the full count. Errors as gz_count.
+ * root range equals the full count. Split thresholds left at 0 (and not set by
+ * gz_autotune) are chosen per query: a query with fewer than 64 work units per
+ * resident warp defers units from 4 loop-2 candidates on in one-candidate work
+ * items when each candidate carries degree-sized work (a flattened subtraction
+ * loop, or k >= 5), else from 64 candidates in items of 64; wider queries defer
+ * from 512 candidates in items of 256. Errors as gz_count.
  */
 gz_status gz_count_ex(const gz_plan* p, const gz_graph* g, const gz_count_opts* opts,
                       void* stream, uint64_t* out_count);
@@ -308,7 +313,8 @@ gz_status gz_count_batch_ranges(const gz_plan* const* plans, const gz_graph* con
  * is one pass of coordinate descent from the defaults over the units per queue
  * pop (1..16), the warps per CTA (4 or 8) and, for k >= 4, the split pass's
  * thresholds: the loop-2 candidate count from which a work unit is deferred to
- * the split pass (128..4096) and the candidates per split work item (64..512).
+ * the split pass (4..4096) and the candidates per split work item (1..256),
+ * starting from the automatic choice described at gz_count_opts.
  * The choices are written to the non-NULL outputs. The count never depends on
  * them. Entries are keyed by the plan's program and a process-unique graph id,
  * and a graph's entries are dropped when it is destroyed.

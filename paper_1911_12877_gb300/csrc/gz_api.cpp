@@ -953,6 +953,7 @@ gz_status gz_autotune(const gz_plan* p, const gz_graph* g, int use_orientation, 
     // coordinate descent from the defaults: units per queue pop, warps per
     // CTA, then the split pass's thresholds (plans with k >= 4 only)
     LaunchCfg best = default_cfg();
+    auto_split(*q.prog, q.unit_hi - q.unit_lo, resident_warps(best), &best.split_min, &best.split_chunk);
     double best_ms = 0.0;
     // oriented cliques run on the clique kernels, which take none of these settings
     const bool clique = clique_eligible(*q.prog, *p, *q.view) && q.view->max_out <= kCliqueLongOut;
@@ -974,8 +975,8 @@ gz_status gz_autotune(const gz_plan* p, const gz_graph* g, int use_orientation, 
         try_values([](LaunchCfg& c, int64_t v) { c.chunk = (int)v; }, {1, 2, 8, 16});
         try_values([](LaunchCfg& c, int64_t v) { c.block_warps = (int)v; }, {4});
         if (p->k >= 4) {
-            try_values([](LaunchCfg& c, int64_t v) { c.split_min = v; }, {128, 256, 1024, 4096});
-            try_values([](LaunchCfg& c, int64_t v) { c.split_chunk = v; }, {64, 128, 512});
+            try_values([](LaunchCfg& c, int64_t v) { c.split_min = v; }, {4, 16, 128, 512, 4096});
+            try_values([](LaunchCfg& c, int64_t v) { c.split_chunk = v; }, {1, 8, 64, 256});
         }
     }
     cudaEventDestroy(ev[0]);

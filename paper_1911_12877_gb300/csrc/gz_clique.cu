@@ -269,34 +269,77 @@ __global__ void __launch_bounds__(kRowsThreads) k_clique_rows(const int64_t* __r
             while (atomicCAS(&hx[sl], ~0ull, kv) != ~0ull) sl = (sl + 1) & kMask;
         }
         __syncthreads();
-        for (;;) {
+        // the next row and its out-list bounds are fetched one row ahead, so
+        // those loads overlap the current row's work
+        int a = -1;
+        int64_t ub = 0, ue = 0;
+        {
             int m = 0;
             if (lane == 0) m = atomicAdd(&s_next, 1);
-            m = __shfl_sync(kFull, m, 0);
-            const int a = d - 1 - m;
-            if (a < 0) break;
+            a = d - 1 - __shfl_sync(kFull, m, 0);
+            if (a >= 0) {
+                ub = drp[O[a]];
+                ue = drp[O[a] + 1];
+            }
+        }
+        while (a >= 0) {
+            int m = 0;
+            if (lane == 0) m = atomicAdd(&s_next, 1);
+            const int an = d - 1 - __shfl_sync(kFull, m, 0);
+            int64_t ubn = 0, uen = 0;
+            if (an >= 0) {
+                ubn = drp[O[an]];
+                uen = drp[O[an] + 1];
+            }
             for (int w = lane; w < Ws; w += 32) rbuf[w] = 0u;
             __syncwarp();
-            const int32_t u = O[a];
-            const int64_t ub = drp[u];
-            const int du = (int)(drp[u + 1] - ub);
+            const int du = (int)(ue - ub);
             if (du <= 4 * a) {
-                for (int i = lane; i < du; i += 32) {
-                    const int32_t x = __ldg(dcol + ub + i);
-                    unsigned sl = ((uint32_t)x * 0x9E3779B1u) >> 21;
-                    int b = -1;
-                    for (;;) {
-                        const unsigned long long e = hx[sl];
-                        if (e == ~0ull) break;
-                        if ((int32_t)(e >> 32) == x) { b = (int)(uint32_t)e; break; }
-                        sl = (sl + 1) & kMask;
+                // stream N'(O[a]) with four loads in flight per lane, probing
+                // the hash of O once per entry
+                for (int i0 = 0; i0 < du; i0 += 128) {
+                    int32_t x[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int i = i0 + 32 * t + lane;
+                        x[t] = i < du ? __ldg(dcol + ub + i) : -1;
                     }
-                    if (b >= 0 && b < a) atomicOr(rbuf + (b >> 5), 1u << (b & 31));
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        if (x[t] < 0) continue;
+                        unsigned sl = ((uint32_t)x[t] * 0x9E3779B1u) >> 21;
+                        int b = -1;
+                        for (;;) {
+                            const unsigned long long e = hx[sl];
+                            if (e == ~0ull) break;
+                            if ((int32_t)(e >> 32) == x[t]) { b = (int)(uint32_t)e; break; }
+                            sl = (sl + 1) & kMask;
+                        }
+                        if (b >= 0 && b < a) atomicOr(rbuf + (b >> 5), 1u << (b & 31));
+                    }
                 }
             } else {
+                // N'(O[a]) is long: look each O[b], b < a, up in it. Sample k of
+                // the list (lane k, one load) is entry p(k) = min(k gap, du - 1),
+                // gap = ceil(du / 32); with k samples <= x, x can only sit in
+                // [p(k - 1), p(k - 1) + gap), which a bisection searches.
+                const int gap = (du + 31) >> 5;
+                const int32_t samp = __ldg(dcol + ub + min(lane * gap, du - 1));
                 for (int b0 = 0; b0 < a; b0 += 32) {
                     const int b = b0 + lane;
-                    const bool in = b < a && has(dcol + ub, du, O[b]);
+                    const int32_t x = b < a ? O[b] : INT32_MAX;
+                    int k = 0;  // samples <= x (samples are nondecreasing)
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const int32_t y = __shfl_sync(kFull, samp, k + step - 1);
+                        if (y <= x) k += step;
+                    }
+                    if (__shfl_sync(kFull, samp, k) <= x) ++k;  // k <= 31 before, may reach 32
+                    bool in = false;
+                    if (b < a && k > 0) {
+                        const int lo = min((k - 1) * gap, du - 1);
+                        in = has(dcol + ub + lo, min(gap, du - lo), x);
+                    }
                     const uint32_t msk = __ballot_sync(kFull, in);
                     if (lane == 0) rbuf[b0 >> 5] = msk;
                 }
@@ -304,6 +347,9 @@ __global__ void __launch_bounds__(kRowsThreads) k_clique_rows(const int64_t* __r
             __syncwarp();
             for (int w = lane; w < Ws; w += 32) dst[(size_t)a * Ws + w] = rbuf[w];
             __syncwarp();
+            a = an;
+            ub = ubn;
+            ue = uen;
         }
         __syncthreads();
     }
@@ -443,11 +489,11 @@ __global__ void __launch_bounds__(kBigThreads) k_clique_big(const int64_t* __res
 // first, heaviest first, with their prebuilt rows; no root is split over CTAs:
 // on the skewed graphs measured the largest root holds a fifth of one SM's
 // share of the work). The CTA's warps pop the root's rows a from a counter in
-// shared memory, largest a first; for its row a, a warp walks the pairs
-// (a, b in row(a)) 32 at a time, one pair per lane. For K = 5 a lane finds its
-// b from the popcount prefix of row(a)'s words (one word per lane, computed once
-// per row) by a shuffle search; for K = 4, whose pairs are cheap, lane l simply
-// takes bit l of each word of row(a). Then the lane counts its pair:
+// shared memory, largest a first, and walk the pairs (a, b in row(a)) one pair
+// per lane: for K = 5, 32 consecutive pairs at a time, a group running on into
+// the next row the warp pops (k5_rows_packed); for K = 4, whose pairs are cheap,
+// lane l simply takes bit l of each word of row(a). Then the lane counts its
+// pair:
 //  - K = 4: |row(a) & row(b)| below b;
 //  - K = 5: with S = row(a) & row(b) (bits below b) held in registers, the sum
 //    over c in S of |S & row(c)|, row(c) holding bits below c only.
@@ -493,7 +539,13 @@ __device__ __forceinline__ uint32_t k4_pair(const uint4* __restrict__ rows4, int
     return cnt;
 }
 
+// Words of S (from word 0) that take the dense walk when they are dense, and
+// the bit count above which a warp counts a word as dense.
+constexpr int kDenseWords = 2;
+constexpr int kDenseMin = 15;
+
 // WM: a multiple of 4 with WM >= ceil(b / 32); S is unrolled into WM registers.
+// Every lane of the warp calls it (b = 0 gives an empty S and no loads).
 template <int WM>
 __device__ __forceinline__ uint32_t k5_pair(const uint4* __restrict__ rows4, int Ws4, int a, int b) {
     const uint4* ra = rows4 + (size_t)a * Ws4;
@@ -514,10 +566,63 @@ __device__ __forceinline__ uint32_t k5_pair(const uint4* __restrict__ rows4, int
     }
     // c runs over the bits of S word w (highest first, one count-leading-zeros
     // each); row(c) is zero above word w, so exactly w + 1 words are counted
-    // (the guards are compile-time constants of the unrolled loops)
+    // (the guards are compile-time constants of the unrolled loops). Words 0..3
+    // hold most candidates on skewed graphs (low local index = high degree);
+    // there row(c) is one 16-byte chunk, loaded one candidate ahead so that the
+    // load of the next row overlaps the popcounts of this one.
     uint32_t cnt = 0;
+    const uint32_t* rows32 = reinterpret_cast<const uint32_t*>(rows4);
+    const int Ws = Ws4 * 4;
 #pragma unroll
-    for (int w = 0; w < WM; ++w) {
+    for (int w = 0; w < 4 && w < WM; ++w) {
+        if (w < kDenseWords) {
+            // Dense word (some lane's S word holds more than kDenseMin bits):
+            // the lanes walk all 32 candidates c = 32 w + j in lockstep, with no
+            // bit search; row(c) is at one address for every lane (a broadcast
+            // load), read only by lanes whose S has bit c (so c < b < d).
+            const unsigned mx = __reduce_max_sync(kFull, (unsigned)__popc(S[w]));
+            if (mx > (unsigned)kDenseMin) {
+#pragma unroll
+                for (int j = (w == 0 ? 1 : 0); j < 32; ++j) {
+                    if ((S[w] >> j) & 1u) {
+                        const uint32_t* rc = rows32 + (size_t)(32 * w + j) * Ws;
+                        if (w == 0) {
+                            cnt += __popc(S[0] & rc[0]);
+                        } else if (w == 1) {
+                            const uint2 r = *reinterpret_cast<const uint2*>(rc);
+                            cnt += __popc(S[0] & r.x) + __popc(S[1] & r.y);
+                        } else {
+                            const uint4 r = *reinterpret_cast<const uint4*>(rc);
+                            cnt += __popc(S[0] & r.x) + __popc(S[1] & r.y) + __popc(S[2] & r.z);
+                            if (w == 3) cnt += __popc(S[3] & r.w);
+                        }
+                    }
+                }
+                continue;
+            }
+        }
+        uint32_t bits = S[w];
+        if (!bits) continue;
+        int hb = 31 - __clz(bits);
+        bits ^= 1u << hb;
+        uint4 r = rows4[(size_t)((w << 5) + hb) * Ws4];
+        while (bits) {
+            hb = 31 - __clz(bits);
+            bits ^= 1u << hb;
+            const uint4 nx = rows4[(size_t)((w << 5) + hb) * Ws4];
+            cnt += __popc(S[0] & r.x);
+            if (w >= 1) cnt += __popc(S[1] & r.y);
+            if (w >= 2) cnt += __popc(S[2] & r.z);
+            if (w >= 3) cnt += __popc(S[3] & r.w);
+            r = nx;
+        }
+        cnt += __popc(S[0] & r.x);
+        if (w >= 1) cnt += __popc(S[1] & r.y);
+        if (w >= 2) cnt += __popc(S[2] & r.z);
+        if (w >= 3) cnt += __popc(S[3] & r.w);
+    }
+#pragma unroll
+    for (int w = 4; w < WM; ++w) {
         uint32_t bits = S[w];
         while (bits) {
             const int hb = 31 - __clz(bits);
@@ -543,6 +648,70 @@ __device__ __forceinline__ uint32_t k5_pair_any(const uint4* rows4, int Ws4, int
     if (nw <= 16) return k5_pair<16>(rows4, Ws4, a, b);
     if (nw <= 24) return k5_pair<24>(rows4, Ws4, a, b);
     return k5_pair<32>(rows4, Ws4, a, b);
+}
+
+// K = 5 walk of one root's rows by one warp. The 32 lanes take 32 consecutive
+// pairs (a, b) in the order: rows a popped from *next (largest a first), bits b
+// of row(a) ascending. A group that exhausts its row continues with the next
+// row the warp pops, so lanes idle only at the end of the root's rows (rows
+// with fewer than 32 bits are the common case on skewed graphs). A lane finds
+// its b from the popcount prefix of row(a)'s words (one word per lane) by a
+// shuffle search. All loop control is warp-uniform.
+__device__ __forceinline__ void k5_rows_packed(const uint32_t* rows, const uint4* rows4, int Ws, int Ws4,
+                                               int d, int lane, int* next, unsigned long long& acc) {
+    int cur_a = 0, cur_j = 0, cur_total = 0;  // row being drawn, pairs taken, its pairs
+    uint32_t word = 0;                        // this lane's word of row(cur_a)
+    int incl = 0;                             // popcount of row(cur_a)'s words 0..lane
+    bool drained = false;
+    for (;;) {
+        int my_a = -1, my_b = 0, filled = 0;
+        while (filled < 32) {
+            if (cur_j == cur_total) {
+                if (drained) break;
+                int m = 0;
+                if (lane == 0) m = atomicAdd(next, 1);
+                m = __shfl_sync(kFull, m, 0);
+                const int a = d - 1 - m;
+                if (a < 1) {
+                    drained = true;
+                    break;
+                }
+                cur_a = a;
+                cur_j = 0;
+                word = lane < ((a + 31) >> 5) ? rows[(size_t)a * Ws + lane] : 0u;
+                incl = __popc(word);
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                cur_total = __shfl_sync(kFull, incl, 31);
+                continue;
+            }
+            const int take = min(32 - filled, cur_total - cur_j);
+            const bool mine = lane >= filled && lane < filled + take;
+            const int j = mine ? cur_j + lane - filled : 0;  // this lane's bit of row(cur_a), in order
+            int wlo = 0, whi = 31;                           // first word whose inclusive count exceeds j
+#pragma unroll
+            for (int step = 0; step < 5; ++step) {
+                const int mid = (wlo + whi) >> 1;
+                const int x = __shfl_sync(kFull, incl, mid);
+                if (x > j) whi = mid; else wlo = mid + 1;
+            }
+            const uint32_t ww = __shfl_sync(kFull, word, wlo);
+            const int before = __shfl_sync(kFull, incl, wlo) - __popc(ww);
+            if (mine) {
+                my_a = cur_a;
+                my_b = (wlo << 5) + select_bit(ww, j - before);
+            }
+            filled += take;
+            cur_j += take;
+        }
+        if (filled == 0) break;
+        // idle lanes (the root's last group) count the empty pair (a, 0)
+        if (my_a < 0) my_a = my_b = 0;
+        const int nw = __reduce_max_sync(kFull, (unsigned)((my_b + 31) >> 5));
+        acc += k5_pair_any(rows4, Ws4, my_a, my_b, nw);
+    }
 }
 
 template <int K>
@@ -606,43 +775,22 @@ __global__ void __launch_bounds__(kWarpCta, 2) k_clique_warp(const int64_t* __re
             __syncthreads();
             const uint4* rows4 = reinterpret_cast<const uint4*>(rows);
             const int Ws4 = Ws >> 2;
-            for (;;) {
-                int m = 0;
-                if (lane == 0) m = atomicAdd(&s_next, 1);
-                m = __shfl_sync(kFull, m, 0);
-                const int a = d - 1 - m;  // largest rows first
-                if (a < 1) break;
-                if constexpr (K == 4) {
-                    // rows are dense on the heavy roots: lane l takes bit l of each
-                    // word w of row(a) (b = 32 w + l), so b needs no search and all
-                    // active lanes count the same w + 1 words
+            if constexpr (K == 5) {
+                k5_rows_packed(rows, rows4, Ws, Ws4, d, lane, &s_next, acc);
+            } else {
+                for (;;) {
+                    int m = 0;
+                    if (lane == 0) m = atomicAdd(&s_next, 1);
+                    m = __shfl_sync(kFull, m, 0);
+                    const int a = d - 1 - m;  // largest rows first
+                    if (a < 1) break;
+                    // rows are dense on the heavy roots, so lane l takes bit l of
+                    // each word w of row(a) (b = 32 w + l): b needs no search and
+                    // all active lanes count the same w + 1 words
                     for (int w = 0, nwa = (a + 31) >> 5; w < nwa; ++w) {
                         const uint32_t bits = rows[(size_t)a * Ws + w];
                         if ((bits >> lane) & 1u) acc += k4_pair(rows4, Ws4, a, (w << 5) + lane);
                     }
-                    continue;
-                }
-                const uint32_t word = lane < ((a + 31) >> 5) ? rows[(size_t)a * Ws + lane] : 0u;
-                int incl = __popc(word);
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int t = __shfl_up_sync(kFull, incl, o);
-                    if (lane >= o) incl += t;
-                }
-                const int total = __shfl_sync(kFull, incl, 31);
-                for (int base = 0; base < total; base += 32) {
-                    const int j = base + lane;  // this lane's bit of row(a), in order
-                    int wlo = 0, whi = 31;      // first word whose inclusive count exceeds j
-#pragma unroll
-                    for (int step = 0; step < 5; ++step) {
-                        const int mid = (wlo + whi) >> 1;
-                        const int x = __shfl_sync(kFull, incl, mid);
-                        if (x > j) whi = mid; else wlo = mid + 1;
-                    }
-                    const uint32_t ww = __shfl_sync(kFull, word, wlo);
-                    const int before = __shfl_sync(kFull, incl, wlo) - __popc(ww);
-                    const int b = j < total ? (wlo << 5) + select_bit(ww, j - before) : 0;
-                    const int nw = __reduce_max_sync(kFull, (unsigned)((b + 31) >> 5));
-                    if (j < total) acc += k5_pair_any(rows4, Ws4, a, b, nw);
                 }
             }
             __syncthreads();

@@ -973,6 +973,12 @@ void fill_kq(const Query& Q, const LaunchCfg& cfg, KQ& k, uint64_t* words_out) {
     memset(&k, 0, sizeof(KQ));
     k.split_min = Q.split_min > 0 ? Q.split_min : cfg.split_min;
     k.split_chunk = Q.split_chunk > 0 ? Q.split_chunk : cfg.split_chunk;
+    if (k.split_min <= 0 || k.split_chunk <= 0) {
+        int64_t smin = 0, sch = 0;
+        auto_split(*Q.prog, Q.unit_hi - Q.unit_lo, resident_warps(cfg), &smin, &sch);
+        if (k.split_min <= 0) k.split_min = smin;
+        if (k.split_chunk <= 0) k.split_chunk = sch;
+    }
     if (k.split_chunk < 1) k.split_chunk = 1;
     k.prog = *Q.prog;
     const GzView& v = *Q.view;
@@ -1044,6 +1050,32 @@ inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 inline int64_t defer_cap(int64_t units) { return std::min<int64_t>(units, (int64_t)1 << 20); }
 
 }  // namespace
+
+// A unit goes to the split pass from split_min loop-2 candidates on and is cut
+// into work items of split_chunk candidates; every item recomputes loop 1. A
+// query with many units per resident warp keeps few, coarse items (512, 256):
+// its heavy units end while the others still run. A query with few units per
+// warp (a narrow root range, a small graph) ends on the critical path of its
+// heaviest units, so it cuts them finely: to single candidates when each
+// loop-2 candidate carries work that grows with its degree (a flattened last
+// loop that streams N(c) against fixed lists, or loops below loop 2), to items
+// of 64 from 64 candidates on for k = 4 patterns whose last loop intersects
+// with a fixed operand. Measured on GB300 on the oracle's sampled R-MAT 22
+// ranges (against (512, 256): tailed triangle 18x, chordal 5-cycle 9x, diamond
+// 1.8x, c4 1.2x faster) and on full R-MAT 16 and 18 counts (where (512, 256)
+// is the fastest or within noise of it).
+constexpr int64_t kNarrowUnitsPerWarp = 64;
+
+void auto_split(const GzProg& p, int64_t units, int warps, int64_t* split_min, int64_t* split_chunk) {
+    if (units < kNarrowUnitsPerWarp * (int64_t)std::max(warps, 1)) {
+        const bool per_candidate_heavy = p.flat == 2 || p.k >= 5;
+        *split_min = per_candidate_heavy ? 4 : 64;
+        *split_chunk = per_candidate_heavy ? 1 : 64;
+    } else {
+        *split_min = 512;
+        *split_chunk = 256;
+    }
+}
 
 // Bytes of a single-query region before its scratch: the counters, then (with
 // splitting) the deferred records and the chunk prefix.
@@ -1316,8 +1348,15 @@ gz_status count_merged(const GzMerged& m, const gz_graph* g, const GzView* v, co
         else { k.usrc = v->src; k.ucol = v->col; k.urp = v->rp; }
         k.unit_lo = 0;
         k.unit_count = units;
-        k.split_min = cfg.split_min;
-        k.split_chunk = cfg.split_chunk > 0 ? cfg.split_chunk : 1;
+        int64_t smin = cfg.split_min, sch = cfg.split_chunk;
+        if (smin <= 0 || sch <= 0) {
+            int64_t a = 0, b = 0;
+            auto_split(k.prog, units, resident_warps(cfg), &a, &b);
+            if (smin <= 0) smin = a;
+            if (sch <= 0) sch = b;
+        }
+        k.split_min = smin;
+        k.split_chunk = sch > 0 ? sch : 1;
         k.out_slot = i == 0 ? 0 : m.plan_index[i - 1];
         k.merge_pos = i == 0 ? 0 : i - 1;
         k.shared_mask = i == 0 ? (m.shared.nops >= 64 ? ~0ull : (1ull << m.shared.nops) - 1)

@@ -191,8 +191,8 @@ struct LaunchCfg {
     int block_warps = 8;     // warps per CTA
     int chunk = 4;           // work units per queue pop
     int blocks = 0;          // 0 = auto (resident CTAs on every SM)
-    int64_t split_min = 512;   // loop-2 candidates from which a unit goes to the split pass
-    int64_t split_chunk = 256; // loop-2 candidates per split-pass work item
+    int64_t split_min = 0;     // loop-2 candidates from which a unit goes to the split pass (0 = auto_split)
+    int64_t split_chunk = 0;   // loop-2 candidates per split-pass work item (0 = auto_split)
     double grid_frac = 1.0;    // < 1: grids take this share of the resident CTAs only
 };
 uint64_t scratch_words_per_warp(const GzProg& p, const gz_graph& g, const GzView& v);
@@ -203,6 +203,9 @@ gz_status count_launch(const Query* qs, int nq, const LaunchCfg& cfg, cudaStream
                        unsigned long long* d_counts, void* scratch, uint64_t scratch_bytes,
                        int* d_status, void* meta, uint64_t meta_bytes);
 int resident_warps(const LaunchCfg& cfg);
+// Split thresholds of a query with this program and number of work units when
+// neither the caller nor the autotuner set them (see gz_count.cu).
+void auto_split(const GzProg& p, int64_t units, int warps, int64_t* split_min, int64_t* split_chunk);
 
 // Bytes of counters (queue, count, status) at the start of a count region.
 constexpr uint64_t kRegionHeader = 256;

@@ -159,7 +159,7 @@ def test_autotune_keeps_count(name):
     assert gz.count(p, G, True) == want
     t = gz.autotune(p, G, True)
     assert t["block_warps"] in (4, 8) and t["chunk"] in (1, 2, 4, 8, 16)
-    assert t["split_min"] in (128, 256, 512, 1024, 4096) and t["split_chunk"] in (64, 128, 256, 512)
+    assert t["split_min"] in (4, 16, 64, 128, 512, 4096) and t["split_chunk"] in (1, 8, 64, 256)
     assert gz.count(p, G, True) == want  # single count with the tuned settings
     # a batch with the tuned query beside untuned ones
     q = gz.Plan("triangle")
