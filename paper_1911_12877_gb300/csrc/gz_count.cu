@@ -1348,13 +1348,14 @@ gz_status count_merged(const GzMerged& m, const gz_graph* g, const GzView* v, co
         else { k.usrc = v->src; k.ucol = v->col; k.urp = v->rp; }
         k.unit_lo = 0;
         k.unit_count = units;
+        // a merged split item re-runs the shared loop-1 operations its plan
+        // reads, so narrow launches split less finely than single programs:
+        // (128, 64), measured on R-MAT 12 motif-4/5 sets against (512, 256),
+        // (64, 16) and (16, 4)
         int64_t smin = cfg.split_min, sch = cfg.split_chunk;
-        if (smin <= 0 || sch <= 0) {
-            int64_t a = 0, b = 0;
-            auto_split(k.prog, units, resident_warps(cfg), &a, &b);
-            if (smin <= 0) smin = a;
-            if (sch <= 0) sch = b;
-        }
+        const bool narrow = units < kNarrowUnitsPerWarp * (int64_t)resident_warps(cfg);
+        if (smin <= 0) smin = narrow ? 128 : 512;
+        if (sch <= 0) sch = narrow ? 64 : 256;
         k.split_min = smin;
         k.split_chunk = sch > 0 ? sch : 1;
         k.out_slot = i == 0 ? 0 : m.plan_index[i - 1];

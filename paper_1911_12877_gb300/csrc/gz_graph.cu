@@ -129,6 +129,9 @@ __global__ void radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shi
 // Stable scatter of one tile. Warp w owns items [w*512, (w+1)*512) of the tile
 // and walks them in order, 32 at a time; __match_any_sync groups equal digits,
 // so ranks follow item order within the warp, and warps are ordered by index.
+// The tile is first reordered by digit in shared memory, then written out
+// run by run: consecutive threads write consecutive slots of one digit's run,
+// so the stores fill whole sectors instead of one or two words per bucket.
 __global__ void radix_scatter(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
                               uint32_t* __restrict__ okeys, uint32_t* __restrict__ ovals,
                               int64_t n, int shift, const int64_t* __restrict__ offs,
@@ -138,11 +141,14 @@ __global__ void radix_scatter(const uint32_t* __restrict__ keys, const uint32_t*
     constexpr int kSteps = kPerWarp / 32;     // 16
     __shared__ uint32_t cnt[kWarps][256];
     __shared__ int64_t base_off[256];
+    __shared__ uint32_t tstart[256];          // first slot of each digit in the reordered tile
+    __shared__ uint32_t sk[kTile], sv[kTile];
     for (int i = threadIdx.x; i < kWarps * 256; i += kThreads) (&cnt[0][0])[i] = 0;
     for (int i = threadIdx.x; i < 256; i += kThreads) base_off[i] = offs[(int64_t)i * ntiles + blockIdx.x];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t wbase = (int64_t)blockIdx.x * kTile + (int64_t)warp * kPerWarp;
+    const int64_t tbase = (int64_t)blockIdx.x * kTile;
+    const int64_t wbase = tbase + (int64_t)warp * kPerWarp;
     uint32_t k[kSteps], v[kSteps], r[kSteps];
 #pragma unroll
     for (int st = 0; st < kSteps; ++st) {
@@ -161,13 +167,35 @@ __global__ void radix_scatter(const uint32_t* __restrict__ keys, const uint32_t*
         __syncwarp();
     }
     __syncthreads();
-    // exclusive prefix over warps per digit
+    // exclusive prefix over warps per digit; the digit's tile total goes to tstart
     for (int d = threadIdx.x; d < 256; d += kThreads) {
         uint32_t run = 0;
         for (int w = 0; w < kWarps; ++w) {
             uint32_t c = cnt[w][d];
             cnt[w][d] = run;
             run += c;
+        }
+        tstart[d] = run;
+    }
+    __syncthreads();
+    if (warp == 0) {  // exclusive scan of the 256 digit totals, 8 per lane
+        uint32_t t[8], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            t[j] = tstart[lane * 8 + j];
+            sum += t[j];
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        uint32_t run = incl - sum;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            tstart[lane * 8 + j] = run;
+            run += t[j];
         }
     }
     __syncthreads();
@@ -176,17 +204,29 @@ __global__ void radix_scatter(const uint32_t* __restrict__ keys, const uint32_t*
         int64_t idx = wbase + st * 32 + lane;
         if (idx < n) {
             uint32_t dg = (k[st] >> shift) & 255u;
-            int64_t pos = base_off[dg] + cnt[warp][dg] + r[st];
-            okeys[pos] = k[st];
-            ovals[pos] = v[st];
+            uint32_t lp = tstart[dg] + cnt[warp][dg] + r[st];
+            sk[lp] = k[st];
+            sv[lp] = v[st];
         }
+    }
+    __syncthreads();
+    const int tn = (int)min((int64_t)kTile, n - tbase);
+    for (int i = threadIdx.x; i < tn; i += kThreads) {
+        const uint32_t kk = sk[i];
+        const uint32_t dg = (kk >> shift) & 255u;
+        const int64_t pos = base_off[dg] + (int64_t)(i - (int)tstart[dg]);
+        okeys[pos] = kk;
+        ovals[pos] = sv[i];
     }
 }
 
-// Stable sort of (key, value) pairs by the low `bits` bits of key. The result
-// ends in (k0, v0); (k1, v1) is scratch of the same size.
+// Stable sort of (key, value) pairs by the low `bits` bits of key, ping-ponging
+// between (k0, v0) and (k1, v1): *rk, *rv receive the pair that holds the
+// result (no copy back), the other pair is scratch afterwards.
 cudaError_t radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t n,
-                             int bits, cudaStream_t s) {
+                             int bits, cudaStream_t s, uint32_t** rk, uint32_t** rv) {
+    *rk = k0;
+    *rv = v0;
     if (n <= 1 || bits <= 0) return cudaSuccess;
     int64_t ntiles = (n + kTile - 1) / kTile;
     int64_t* hist = nullptr;
@@ -205,12 +245,8 @@ cudaError_t radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t*
         std::swap(k0, k1);
         std::swap(v0, v1);
     }
-    if (e == cudaSuccess && (passes & 1)) {
-        // result sits in the scratch pair; copy it back
-        e = cudaMemcpyAsync(k1, k0, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(v1, v0, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
-    }
+    *rk = k0;
+    *rv = v0;
     cudaFreeAsync(hist, s);
     return e;
 }
@@ -316,12 +352,15 @@ __global__ void k_check_segments(const uint32_t* __restrict__ keys, const int64_
     }
 }
 
-// split[v] = |N(v) intersect [0, v)| (lists sorted): one warp per vertex.
+// split[v] = |N(v) intersect [0, v)| (lists sorted): one warp per vertex. The
+// largest split goes to *maxout by one atomic per warp (a per-vertex atomic on
+// one address serialises in L2).
 __global__ void k_split(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, int64_t n,
                         int64_t* __restrict__ split, unsigned long long* __restrict__ maxout) {
     const int lane = threadIdx.x & 31;
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t wmax = 0;
     for (int64_t v = warp; v < n; v += nwarps) {
         int64_t b = rp[v], e = rp[v + 1];
         int64_t cnt = 0;
@@ -332,11 +371,10 @@ __global__ void k_split(const int64_t* __restrict__ rp, const int32_t* __restric
             if (!__shfl_sync(__activemask(), lt ? 1 : 0, 31 - __clz(__activemask()))) break;
         }
         cnt = __shfl_sync(0xffffffffu, cnt, 0);
-        if (lane == 0) {
-            split[v] = cnt;
-            if (cnt > 0) atomicMax(maxout, (unsigned long long)cnt);
-        }
+        if (lane == 0) split[v] = cnt;
+        wmax = cnt > wmax ? cnt : wmax;
     }
+    if (lane == 0 && wmax > 0) atomicMax(maxout, (unsigned long long)wmax);
 }
 
 __global__ void k_dag_fill(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
@@ -544,33 +582,32 @@ gz_status orient(gz_graph* g, cudaStream_t s) {
         cudaMemsetAsync(bad, 0, sizeof(unsigned long long), s);
         k_rank_keys<<<grid_for(n, kThreads), kThreads, 0, s>>>(deg, n, g->max_deg, k0, v0);
         GZ_COUNT_LAUNCH();
-        e = radix_sort_pairs(k0, v0, k1, v1, n, bits_for((uint64_t)g->max_deg), s);
+        uint32_t *rk = nullptr, *order = nullptr;
+        e = radix_sort_pairs(k0, v0, k1, v1, n, bits_for((uint64_t)g->max_deg), s, &rk, &order);
         if (e != cudaSuccess) { st = cuda_fail(e, "gz_orient: rank sort"); goto done; }
-        // 2. new ids and new row pointers (v0 = order: old id per rank)
-        k_new_ids<<<grid_for(n, kThreads), kThreads, 0, s>>>(v0, deg, n, g->new_id, ndeg);
+        // 2. new ids and new row pointers (order: old id per rank)
+        k_new_ids<<<grid_for(n, kThreads), kThreads, 0, s>>>(order, deg, n, g->new_id, ndeg);
         GZ_COUNT_LAUNCH();
         cudaMemsetAsync(ndeg + n, 0, sizeof(int64_t), s);
         e = exclusive_scan(ndeg, o.rp, n + 1, s);
         if (e != cudaSuccess) { st = cuda_fail(e, "gz_orient: row scan"); goto done; }
-        // 3. relabel rows in rank order, then stable sort by neighbour id: each
+        // 3. relabel rows in rank order into the pair that does not hold the
+        //    order, then stable sort by neighbour id (the order's pair is the
+        //    scratch, overwritten only after the relabel, in stream order): each
         //    segment then lists its neighbours' ranks in ascending order.
-        uint32_t* order = v0;
-        // keys/vals for the edge sort reuse k1/v1 and a second pair from k0 after
-        // copying the order out of v0
-        uint32_t* order_copy = nullptr;
-        e = gz_malloc_async(&order_copy, sizeof(uint32_t) * n, s);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(order_copy, order, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
-        if (e != cudaSuccess) { st = cuda_fail(e, "gz_orient: order copy"); goto done; }
-        k_relabel_rows<<<warp_grid(n), kThreads, 0, s>>>(g->orig.rp, g->orig.col, order_copy,
-                                                        g->new_id, o.rp, n, k0, v0);
+        uint32_t* ak = order == v0 ? k1 : k0;
+        uint32_t* av = order == v0 ? v1 : v0;
+        uint32_t* bk = order == v0 ? k0 : k1;
+        uint32_t* bv = order == v0 ? v0 : v1;
+        k_relabel_rows<<<warp_grid(n), kThreads, 0, s>>>(g->orig.rp, g->orig.col, order,
+                                                        g->new_id, o.rp, n, ak, av);
         GZ_COUNT_LAUNCH();
-        cudaFreeAsync(order_copy, s);
-        e = radix_sort_pairs(k0, v0, k1, v1, nnz, bits_for((uint64_t)(n - 1)), s);
+        uint32_t *sk = nullptr, *sv = nullptr;
+        e = radix_sort_pairs(ak, av, bk, bv, nnz, bits_for((uint64_t)(n - 1)), s, &sk, &sv);
         if (e != cudaSuccess) { st = cuda_fail(e, "gz_orient: edge sort"); goto done; }
-        k_check_segments<<<warp_grid(n), kThreads, 0, s>>>(k0, o.rp, n, bad);
+        k_check_segments<<<warp_grid(n), kThreads, 0, s>>>(sk, o.rp, n, bad);
         GZ_COUNT_LAUNCH();
-        e = cudaMemcpyAsync(o.col, v0, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, s);
+        e = cudaMemcpyAsync(o.col, sv, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, s);
         unsigned long long hbad = 0;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
