@@ -271,6 +271,17 @@ gz_status gz_count_noalloc(const gz_plan* p, const gz_graph* g, int use_orientat
                            uint64_t* out_count);
 
 /*
+ * Builds, on `stream`, the device state that counts of this plan on this graph
+ * view read and the library caches (no paper counterpart): the out-list view
+ * and source arrays the plan's loops use and, for oriented k-cliques, the
+ * bitset rows of the roots with 33 to 1024 out-neighbours. A later count then
+ * does only the counting. The state lasts until gz_orient rebuilds the view or
+ * the graph is destroyed; counting without this call builds it on first use.
+ * Synchronous on `stream`. Errors: GZ_EINVAL, GZ_ENOMEM, GZ_ECUDA.
+ */
+gz_status gz_prepare(const gz_plan* p, const gz_graph* g, int use_orientation, void* stream);
+
+/*
  * Device scratch gz_count needs for this plan and graph (bytes), so callers can
  * budget memory before admitting a query.
  */
@@ -333,7 +344,10 @@ gz_status gz_autotune(const gz_plan* p, const gz_graph* g, int use_orientation, 
  * the edges (e0, e1) once, computing those shared sets once per edge and then
  * running each plan's remaining loops against them; a plan's edges with many
  * loop-2 candidates go to a split pass as in gz_count. Oriented k-cliques
- * (use_orientation = 1) run on the bitset clique kernels beside it. The counts
+ * (use_orientation = 1) run on the bitset clique kernels beside it; a K4 and a
+ * K5 plan together, on a view whose out-lists hold at most 1024 vertices, take
+ * one fused clique pass (the K4 loops are a prefix of the K5 loops: each pair's
+ * K4 count is the size of the candidate set the K5 walk forms). The counts
  * equal gz_count's. Errors: GZ_EINVAL, GZ_ENOMEM, GZ_ECUDA.
  */
 gz_status gz_count_merged(const gz_plan* const* plans, int np, const gz_graph* g, int use_orientation,

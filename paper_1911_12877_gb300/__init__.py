@@ -27,7 +27,7 @@ EXPORTS = [
     "gz_load_csr", "gz_orient", "gz_graph_info", "gz_graph_export", "gz_graph_destroy",
     "gz_pattern_named", "gz_plan_create", "gz_plan_create_with_order", "gz_plan_info",
     "gz_plan_schedules", "gz_plan_describe", "gz_plan_destroy", "gz_count", "gz_count_ex", "gz_scratch_bytes",
-    "gz_count_batch", "gz_count_batch_ranges", "gz_count_noalloc", "gz_autotune", "gz_server_create", "gz_server_submit", "gz_server_wait",
+    "gz_count_batch", "gz_count_batch_ranges", "gz_count_noalloc", "gz_prepare", "gz_autotune", "gz_server_create", "gz_server_submit", "gz_server_wait",
     "gz_server_replay", "gz_server_destroy", "gz_last_error", "gz_version", "gz_kernel_launches",
     "gz_allocations", "gz_count_merged",
     "gz_motif_patterns", "gz_count_motifs", "gz_plan_create_measured", "gz_schedule_times",
@@ -96,6 +96,7 @@ def lib() -> ctypes.CDLL:
         "gz_count": [_P, _P, I, _P, _u64p],
         "gz_count_ex": [_P, _P, ctypes.POINTER(CountOpts), _P, _u64p],
         "gz_scratch_bytes": [_P, _P, I, _u64p],
+        "gz_prepare": [_P, _P, I, _P],
         "gz_count_noalloc": [_P, _P, I, _P, _u64p],
         "gz_count_batch": [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(I), I, _P, _u64p],
         "gz_count_batch_ranges": [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(I), _i64p, _i64p, I, _P,
@@ -353,6 +354,12 @@ def count(plan: Plan, graph: Graph, orientation: bool = False, root_lo: int = 0,
     _check(lib().gz_count_ex(plan.handle, graph.handle, ctypes.byref(o), _stream(stream),
                              ctypes.byref(out)), "gz_count")
     return out.value
+
+
+def prepare(plan: Plan, graph: Graph, orientation: bool = False, stream=None) -> None:
+    """gz_prepare: build the cached device state counts of this plan read (views,
+    clique rows), so that a later count does only the counting."""
+    _check(lib().gz_prepare(plan.handle, graph.handle, int(orientation), _stream(stream)), "gz_prepare")
 
 
 def count_noalloc(plan: Plan, graph: Graph, orientation: bool = False, stream=None) -> int:

@@ -735,6 +735,23 @@ gz_status gz_count(const gz_plan* p, const gz_graph* g, int use_orientation, voi
     return gz_count_ex(p, g, &o, stream, out_count);
 }
 
+gz_status gz_prepare(const gz_plan* p, const gz_graph* g, int use_orientation, void* stream) {
+    GZ_RANGE("gz_prepare");
+    if (!p || !check_graph(g, "gz_prepare")) {
+        if (!p) set_error("gz_prepare: plan is NULL");
+        return GZ_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    Query q{};
+    gz_status st = prepare_query(p, g, use_orientation, 0, -1, s, q);
+    if (st != GZ_OK) return st;
+    if (clique_eligible(*q.prog, *p, *q.view) && q.view->max_out <= kCliqueLongOut)
+        st = clique_prepare(*q.view, g->n, s);
+    if (st != GZ_OK) return st;
+    const cudaError_t e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? GZ_OK : cuda_fail(e, "gz_prepare");
+}
+
 gz_status gz_scratch_bytes(const gz_plan* p, const gz_graph* g, int use_orientation, uint64_t* bytes) {
     if (!p || !check_graph(g, "gz_scratch_bytes") || !bytes) return GZ_EINVAL;
     if (use_orientation && !g->oriented) { set_error("gz_scratch_bytes: graph not oriented"); return GZ_EINVAL; }
@@ -841,6 +858,33 @@ gz_status gz_count_merged(const gz_plan* const* plans, int np, const gz_graph* g
             gen_idx.push_back(i);
         }
     }
+    // oriented K4 and K5 on one view: one fused clique pass (the K4 loops are a
+    // prefix of the K5 loops, so the K5 walk forms every K4 candidate set),
+    // placed after the other clique queries
+    bool fuse45 = false;
+    {
+        int f4 = -1, f5 = -1;
+        for (size_t c = 0; c < cliq.size(); ++c) {
+            if (cliq[c].plan->k == 4 && f4 < 0) f4 = (int)c;
+            if (cliq[c].plan->k == 5 && f5 < 0) f5 = (int)c;
+        }
+        if (f4 >= 0 && f5 >= 0 && cliq[f4].view == cliq[f5].view && clique45_fusable(*cliq[f5].view)) {
+            std::vector<Query> q2;
+            std::vector<int> i2;
+            for (size_t c = 0; c < cliq.size(); ++c)
+                if ((int)c != f4 && (int)c != f5) {
+                    q2.push_back(cliq[c]);
+                    i2.push_back(cliq_idx[c]);
+                }
+            q2.push_back(cliq[f4]);
+            i2.push_back(cliq_idx[f4]);
+            q2.push_back(cliq[f5]);
+            i2.push_back(cliq_idx[f5]);
+            cliq.swap(q2);
+            cliq_idx.swap(i2);
+            fuse45 = true;
+        }
+    }
     std::vector<GzMerged> groups;
     gz_status st = merge_plans(plans, gen_idx.data(), (int)gen_idx.size(), groups);
     if (st != GZ_OK) return st;
@@ -888,9 +932,15 @@ gz_status gz_count_merged(const gz_plan* const* plans, int np, const gz_graph* g
         if (st != GZ_OK) break;
         st = count_merged(m, g, v, cfg, t, d, d_status, gs, gscr, gm, gmeta);
     }
-    if (st == GZ_OK && nc > 0)  // clique counts land in their own slots, moved to their plans' below
-        st = launch_mixed(cliq.data(), (int)nc, cfg, s, d + np + 1, d_status, d + np + 1 + nc, cs, cscr, cm,
+    const size_t nc_mixed = fuse45 ? nc - 2 : nc;
+    if (st == GZ_OK && nc_mixed > 0)  // clique counts land in their own slots, moved to their plans' below
+        st = launch_mixed(cliq.data(), (int)nc_mixed, cfg, s, d + np + 1, d_status, d + np + 1 + nc, cs, cscr, cm,
                           cmeta, true);
+    if (st == GZ_OK && fuse45) {  // K4 in slot nc - 2, K5 in slot nc - 1
+        const Query& q5 = cliq[nc - 1];
+        st = clique_launch45(*q5.view, g->n, 0, g->n, cfg.grid_frac, s, d + np + 1 + (nc - 1),
+                             d + np + 1 + (nc - 2), d + np + 1 + nc + kCliqueWork * (nc - 1));
+    }
     if (ev1) {
         cudaEventRecord(ev1, t);
         cudaStreamWaitEvent(s, ev1, 0);

@@ -129,17 +129,21 @@ __device__ __forceinline__ unsigned long long block_sum(unsigned long long v, un
 }
 
 // Roots with 1 <= |O| <= 32: one warp per root, dynamic root queue.
+// count4 (K = 5 only, else NULL): the fused K4 + K5 pass also adds each pair's
+// K4 count |row(a) & row(b)| there.
 template <int K>
 __global__ void __launch_bounds__(kThreads) k_clique_small(const int64_t* __restrict__ drp,
                                                            const int32_t* __restrict__ dcol,
                                                            int64_t root_lo, int64_t root_hi,
                                                            unsigned long long* __restrict__ work,
-                                                           unsigned long long* __restrict__ count) {
+                                                           unsigned long long* __restrict__ count,
+                                                           unsigned long long* __restrict__ count4) {
     __shared__ uint32_t rows_s[kThreads / 32][32];
     __shared__ unsigned long long red[kThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t* rows = rows_s[warp];
-    unsigned long long acc = 0;
+    unsigned long long acc = 0, acc4 = 0;
+    const int dmin = count4 ? 3 : K - 1;
     for (;;) {
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(work, 32ull);
@@ -151,7 +155,7 @@ __global__ void __launch_bounds__(kThreads) k_clique_small(const int64_t* __rest
             if (v >= root_hi) break;
             const int64_t ob = drp[v];
             const int d = (int)(drp[v + 1] - ob);
-            if (d < K - 1 || d > 32) continue;
+            if (d < dmin || d > 32) continue;
             const int32_t u = lane < d ? dcol[ob + lane] : 0;
             const int64_t ub = lane < d ? drp[u] : 0;
             const int du = lane < d ? (int)(drp[u + 1] - ub) : 0;
@@ -168,6 +172,7 @@ __global__ void __launch_bounds__(kThreads) k_clique_small(const int64_t* __rest
                     const int b = __ffs(bits) - 1;
                     bits &= bits - 1;
                     acc += count_pair<K>(rows, 1, lane, b);
+                    if (count4) acc4 += __popc(row & rows[b]);
                 }
             }
             __syncwarp();
@@ -175,6 +180,11 @@ __global__ void __launch_bounds__(kThreads) k_clique_small(const int64_t* __rest
     }
     unsigned long long s = block_sum(acc, red);
     if (threadIdx.x == 0 && s) atomicAdd(count, s);
+    if (count4) {
+        __syncthreads();  // red is reused
+        s = block_sum(acc4, red);
+        if (threadIdx.x == 0 && s) atomicAdd(count4, s);
+    }
 }
 
 // Builds row(a), a in [1, d), of the root whose out-list O[0, d) is in shared
@@ -546,8 +556,11 @@ constexpr int kDenseMin = 15;
 
 // WM: a multiple of 4 with WM >= ceil(b / 32); S is unrolled into WM registers.
 // Every lane of the warp calls it (b = 0 gives an empty S and no loads).
-template <int WM>
-__device__ __forceinline__ uint32_t k5_pair(const uint4* __restrict__ rows4, int Ws4, int a, int b) {
+// F4: also add |S| to k4 (the pair's K4 count: S holds the vertices that close
+// a 4-clique with (root, a, b)), for the fused K4 + K5 pass.
+template <int WM, bool F4>
+__device__ __forceinline__ uint32_t k5_pair(const uint4* __restrict__ rows4, int Ws4, int a, int b,
+                                            uint32_t& k4) {
     const uint4* ra = rows4 + (size_t)a * Ws4;
     const uint4* rb = rows4 + (size_t)b * Ws4;
     const int nq = (b + 127) >> 7;
@@ -558,6 +571,7 @@ __device__ __forceinline__ uint32_t k5_pair(const uint4* __restrict__ rows4, int
         if (q < nq) {
             const uint4 A = ra[q], B = rb[q];
             x = make_uint4(A.x & B.x, A.y & B.y, A.z & B.z, A.w & B.w);
+            if constexpr (F4) k4 += __popc(x.x) + __popc(x.y) + __popc(x.z) + __popc(x.w);
         }
         S[4 * q] = x.x;
         S[4 * q + 1] = x.y;
@@ -643,11 +657,12 @@ __device__ __forceinline__ uint32_t k5_pair(const uint4* __restrict__ rows4, int
 
 // nw: words of the widest pair among the warp's active lanes (the same for all
 // lanes, so the warp runs one instantiation of k5_pair).
-__device__ __forceinline__ uint32_t k5_pair_any(const uint4* rows4, int Ws4, int a, int b, int nw) {
-    if (nw <= 8) return k5_pair<8>(rows4, Ws4, a, b);
-    if (nw <= 16) return k5_pair<16>(rows4, Ws4, a, b);
-    if (nw <= 24) return k5_pair<24>(rows4, Ws4, a, b);
-    return k5_pair<32>(rows4, Ws4, a, b);
+template <bool F4>
+__device__ __forceinline__ uint32_t k5_pair_any(const uint4* rows4, int Ws4, int a, int b, int nw, uint32_t& k4) {
+    if (nw <= 8) return k5_pair<8, F4>(rows4, Ws4, a, b, k4);
+    if (nw <= 16) return k5_pair<16, F4>(rows4, Ws4, a, b, k4);
+    if (nw <= 24) return k5_pair<24, F4>(rows4, Ws4, a, b, k4);
+    return k5_pair<32, F4>(rows4, Ws4, a, b, k4);
 }
 
 // K = 5 walk of one root's rows by one warp. The 32 lanes take 32 consecutive
@@ -656,9 +671,11 @@ __device__ __forceinline__ uint32_t k5_pair_any(const uint4* rows4, int Ws4, int
 // row the warp pops, so lanes idle only at the end of the root's rows (rows
 // with fewer than 32 bits are the common case on skewed graphs). A lane finds
 // its b from the popcount prefix of row(a)'s words (one word per lane) by a
-// shuffle search. All loop control is warp-uniform.
+// shuffle search. All loop control is warp-uniform. F4: K4 counts too (acc4).
+template <bool F4>
 __device__ __forceinline__ void k5_rows_packed(const uint32_t* rows, const uint4* rows4, int Ws, int Ws4,
-                                               int d, int lane, int* next, unsigned long long& acc) {
+                                               int d, int lane, int* next, unsigned long long& acc,
+                                               unsigned long long& acc4) {
     int cur_a = 0, cur_j = 0, cur_total = 0;  // row being drawn, pairs taken, its pairs
     uint32_t word = 0;                        // this lane's word of row(cur_a)
     int incl = 0;                             // popcount of row(cur_a)'s words 0..lane
@@ -710,11 +727,14 @@ __device__ __forceinline__ void k5_rows_packed(const uint32_t* rows, const uint4
         // idle lanes (the root's last group) count the empty pair (a, 0)
         if (my_a < 0) my_a = my_b = 0;
         const int nw = __reduce_max_sync(kFull, (unsigned)((my_b + 31) >> 5));
-        acc += k5_pair_any(rows4, Ws4, my_a, my_b, nw);
+        uint32_t k4 = 0;
+        acc += k5_pair_any<F4>(rows4, Ws4, my_a, my_b, nw, k4);
+        if constexpr (F4) acc4 += k4;
     }
 }
 
-template <int K>
+// F4 (K = 5 only): the fused K4 + K5 pass; the K4 count goes to *count4.
+template <int K, bool F4 = false>
 __global__ void __launch_bounds__(kWarpCta, 2) k_clique_warp(const int64_t* __restrict__ drp,
                                                           const int32_t* __restrict__ dcol,
                                                           int64_t root_lo, int64_t root_hi,
@@ -723,8 +743,10 @@ __global__ void __launch_bounds__(kWarpCta, 2) k_clique_warp(const int64_t* __re
                                                           int nheavy,
                                                           const uint32_t* __restrict__ grows,
                                                           unsigned long long* __restrict__ work,
-                                                          unsigned long long* __restrict__ count) {
+                                                          unsigned long long* __restrict__ count,
+                                                          unsigned long long* __restrict__ count4) {
     static_assert(K == 4 || K == 5, "k_clique_warp counts K4 and K5");
+    static_assert(!F4 || K == 5, "the fused pass is the K5 walk");
     extern __shared__ __align__(16) uint32_t smw[];
     __shared__ unsigned long long red[kWarpCtaWarps];
     __shared__ int64_t s_slot;
@@ -733,7 +755,7 @@ __global__ void __launch_bounds__(kWarpCta, 2) k_clique_warp(const int64_t* __re
     uint32_t* rows = smw;
     int32_t* O = reinterpret_cast<int32_t*>(smw + (size_t)max_out * Wsmax);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long acc = 0;
+    unsigned long long acc = 0, acc4 = 0;
     const int64_t nchunks = (root_hi - root_lo + kBigPop - 1) / kBigPop;
     for (;;) {
         // queue slots: [0, nheavy) one heavy root each (heaviest first), then
@@ -776,7 +798,7 @@ __global__ void __launch_bounds__(kWarpCta, 2) k_clique_warp(const int64_t* __re
             const uint4* rows4 = reinterpret_cast<const uint4*>(rows);
             const int Ws4 = Ws >> 2;
             if constexpr (K == 5) {
-                k5_rows_packed(rows, rows4, Ws, Ws4, d, lane, &s_next, acc);
+                k5_rows_packed<F4>(rows, rows4, Ws, Ws4, d, lane, &s_next, acc, acc4);
             } else {
                 for (;;) {
                     int m = 0;
@@ -798,6 +820,11 @@ __global__ void __launch_bounds__(kWarpCta, 2) k_clique_warp(const int64_t* __re
     }
     unsigned long long s = block_sum(acc, red);
     if (threadIdx.x == 0 && s) atomicAdd(count, s);
+    if constexpr (F4) {
+        __syncthreads();  // red is reused
+        s = block_sum(acc4, red);
+        if (threadIdx.x == 0 && s) atomicAdd(count4, s);
+    }
 }
 
 // Roots whose out-list is too long for shared-memory rows (kCliqueMaxOut <
@@ -1208,9 +1235,17 @@ gz_status launch_long(GzView& v, int64_t lo, int64_t hi, double frac, cudaStream
 // request loop runs slow requests on part of the device).
 inline int grid_part(int full, double frac) { return frac < 1.0 ? std::max(1, (int)(full * frac)) : full; }
 
+// d_count4 (K = 5 only, else NULL): the fused K4 + K5 pass, which also adds the
+// K4 count of the roots to *d_count4; the view must have no root longer than
+// kCliqueMaxOut (those take the long-root kernels, which count one K).
 template <int K>
 gz_status launch_k(const GzView& v, int64_t n, int64_t lo, int64_t hi, double frac, cudaStream_t s,
-                   unsigned long long* d_count, unsigned long long* d_work) {
+                   unsigned long long* d_count, unsigned long long* d_work,
+                   unsigned long long* d_count4 = nullptr) {
+    if (d_count4 && (K != 5 || v.max_out > kCliqueMaxOut)) {
+        set_error("fused K4 + K5 pass: needs K = 5 and out-lists of at most %d", kCliqueMaxOut);
+        return GZ_EINVAL;
+    }
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1219,7 +1254,7 @@ gz_status launch_k(const GzView& v, int64_t n, int64_t lo, int64_t hi, double fr
     int blocks = grid_part(sms * (per_sm > 0 ? per_sm : 1), frac);
     const int64_t need_small = (nroots + 32 * (kThreads / 32) - 1) / (32 * (kThreads / 32));
     if (need_small < blocks) blocks = (int)std::max<int64_t>(1, need_small);
-    k_clique_small<K><<<blocks, kThreads, 0, s>>>(v.dag_rp, v.dag_col, lo, hi, d_work, d_count);
+    k_clique_small<K><<<blocks, kThreads, 0, s>>>(v.dag_rp, v.dag_col, lo, hi, d_work, d_count, d_count4);
     GZ_COUNT_LAUNCH();
     if (v.max_out <= 32) {
         cudaError_t e = cudaGetLastError();
@@ -1268,14 +1303,18 @@ gz_status launch_k(const GzView& v, int64_t n, int64_t lo, int64_t hi, double fr
     if (e == cudaSuccess) {
         const int64_t slots = (int64_t)nslots + (nroots + kBigPop - 1) / kBigPop;
         if constexpr (K <= 5) {
-            e = cudaFuncSetAttribute(k_clique_warp<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            auto kern = k_clique_warp<K, false>;
+            if constexpr (K == 5) {
+                if (d_count4) kern = k_clique_warp<5, true>;
+            }
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e == cudaSuccess)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clique_warp<K>, kWarpCta, smem);
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpCta, smem);
             int bb = grid_part(sms * (per_sm > 0 ? per_sm : 1), frac);
             if (slots < bb) bb = (int)std::max<int64_t>(1, slots);
             if (e == cudaSuccess) {
-                k_clique_warp<K><<<bb, kWarpCta, smem, s>>>(v.dag_rp, v.dag_col, lo, hi, mo, heavy_d, d_slots,
-                                                             nslots, mv.heavy_rows, d_work + 1, d_count);
+                kern<<<bb, kWarpCta, smem, s>>>(v.dag_rp, v.dag_col, lo, hi, mo, heavy_d, d_slots, nslots,
+                                                mv.heavy_rows, d_work + 1, d_count, d_count4);
                 GZ_COUNT_LAUNCH();
             }
         } else {
@@ -1340,6 +1379,17 @@ gz_status clique_launch(int k, const GzView& v, int64_t n, int64_t lo, int64_t h
     }
     set_error("clique kernel: k = %d unsupported", k);
     return GZ_EINVAL;
+}
+
+bool clique45_fusable(const GzView& v) { return v.has_dag && v.max_out <= kCliqueMaxOut; }
+
+// The fused K4 + K5 pass: one walk over the pairs (a, b) of every root adds the
+// pair's K5 count to *d_count5 and its K4 count |row(a) & row(b)| to *d_count4
+// (the K4 loops are a prefix of the K5 loops). Requires clique45_fusable(v).
+gz_status clique_launch45(const GzView& v, int64_t n, int64_t lo, int64_t hi, double frac, cudaStream_t s,
+                          unsigned long long* d_count5, unsigned long long* d_count4, unsigned long long* d_work) {
+    if (hi <= lo) return GZ_OK;
+    return launch_k<5>(v, n, lo, hi, frac, s, d_count5, d_work, d_count4);
 }
 
 }  // namespace gz

@@ -265,5 +265,10 @@ uint64_t mixed_meta_bytes(const Query* qs, int nq);
 gz_status clique_prepare(const GzView& v, int64_t n, cudaStream_t s);
 gz_status clique_launch(int k, const GzView& v, int64_t n, int64_t lo, int64_t hi, double frac, cudaStream_t s,
                         unsigned long long* d_count, unsigned long long* d_work);
+// Fused K4 + K5 clique pass (both counts from one walk over the pairs), for
+// views whose longest out-list fits the shared-memory row kernels.
+bool clique45_fusable(const GzView& v);
+gz_status clique_launch45(const GzView& v, int64_t n, int64_t lo, int64_t hi, double frac, cudaStream_t s,
+                          unsigned long long* d_count5, unsigned long long* d_count4, unsigned long long* d_work);
 
 }  // namespace gz

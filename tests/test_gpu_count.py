@@ -389,6 +389,54 @@ def test_cliques_with_out_lists_beyond_the_bitset_limit():
     assert gz.count(gz.Plan("k4"), G, orientation=True) == oracle_count("k4", g)
 
 
+def test_fused_k4_k5_closed_form():
+    """K4 and K5 in one gz_count_merged call take the fused clique pass (one walk
+    over the root pairs yields both counts). Complete 16-partite graph with parts
+    of 60: oriented out-lists up to 900 (rows of 29 words, all in shared memory).
+    A k-clique takes one vertex from each of k parts: C(16, k) * 60^k. A second
+    K4 query and a triangle query ride along on the separate clique kernels."""
+    import math
+    parts, r = 16, 60
+    n = parts * r
+    idx = np.arange(n)
+    src, dst = np.meshgrid(idx, idx, indexing="ij")
+    keep = (src < dst) & (src // r != dst // r)
+    e = np.stack([src[keep], dst[keep]], 1).astype(np.int32)
+    G = gz.Graph.from_csr(S.from_edges(n, e, "K16x60")).orient()
+    assert 32 < G.info()["max_out_degree_oriented"] <= 1024
+    want = {k: math.comb(parts, k) * r ** k for k in (3, 4, 5)}
+    names = ["k4", "k5", "k4", "triangle"]
+    got = gz.count_merged([gz.Plan(x) for x in names], G, orientation=True)
+    assert got == [want[4], want[5], want[4], want[3]]
+    # on an R-MAT graph (roots of every out-degree class up to the longest) the
+    # fused counts equal the oracle's
+    g = S.rmat(13, 16, 53)
+    G2 = gz.Graph.from_csr(g).orient()
+    assert gz.count_merged([gz.Plan("k5"), gz.Plan("k4")], G2, orientation=True) == [
+        oracle_count("k5", g), oracle_count("k4", g)]
+
+
+def test_prepare_then_count():
+    """gz_prepare builds the views and clique rows ahead of the count; counts
+    after it (and after a second prepare, and after reorienting) are the
+    oracle's, and an oriented prepare on a graph never oriented is refused."""
+    g = S.rmat(12, 16, 57)
+    G = gz.Graph.from_csr(g)
+    with pytest.raises(gz.GzError) as e:
+        gz.prepare(gz.Plan("k5"), G, orientation=True)
+    assert e.value.status == gz.GZ_EINVAL
+    G.orient()
+    want = [oracle_count(n, g) for n in ("k4", "k5", "diamond")]
+    plans = [gz.Plan(n) for n in ("k4", "k5", "diamond")]
+    for p in plans:
+        gz.prepare(p, G, orientation=True)
+    gz.prepare(plans[1], G, orientation=True)
+    assert gz.count_merged(plans, G, orientation=True) == want
+    G.orient()
+    gz.prepare(plans[1], G, orientation=True)
+    assert [gz.count(p, G, True) for p in plans] == want
+
+
 def test_cliques_on_multipartite_long_out_lists():
     """Complete 16-partite graph with parts of 75: every vertex has degree 1125,
     so oriented out-lists run past 1024 (the long-root launch of the K4/K5
