@@ -50,3 +50,21 @@ def test_committed_profile_matches_kernel_source():
     d = bench.profiled(bench.PROFILE_K5)
     assert d is not None, "k_clique_warp changed since its ncu capture"
     assert d["dram_bytes_per_launch"] == d["dram_bytes_read"] + d["dram_bytes_write"]
+
+
+def test_clique_roofline_arithmetic():
+    """The fused count's roofline: achieved = the oracle's K4 + K5 bitset word
+    operations / count time; peak = 16 popcounts per clock per SM x SMs x the
+    sampled SM clock; traffic and DRAM fraction from the committed capture."""
+    gold = json.load(open(bench.os.path.join(bench.GOLDEN, "clique_rmat20.json")))
+    words = gold["k4"]["bitset_words"] + gold["k5"]["bitset_words"]
+    prof = {"dram_bytes_per_launch": 470_000_000, "xu_pipe_pct": 40.0, "issue_active_pct": 70.0}
+    r = bench.clique_roofline(words, 0.025, 4.97e12, {"sm_mhz": 2070.0}, 152, prof)
+    peak = 16 * 152 * 2070e6 / 1e9
+    assert r["bound"] == "alu" and r["unit"] == "Gword-op/s"
+    assert r["peak"] == pytest.approx(peak, rel=1e-4)
+    assert r["achieved"] == pytest.approx(words / 0.025 / 1e9, rel=1e-4)
+    assert r["frac"] == pytest.approx(words / 0.025 / 1e9 / peak, abs=1e-4)
+    assert r["traffic"] == 470_000_000
+    assert r["dram_frac"] == pytest.approx(470e6 / 0.025 / 1e9 / bench.measured_peaks()[0], abs=1e-6)
+    assert r["algorithmic_words"] == words
