@@ -292,8 +292,9 @@ gz_status gz_scratch_bytes(const gz_plan* p, const gz_graph* g, int use_orientat
  * Batched counting: nq independent (plan, graph, use_orientation[i]) queries in
  * one call (no paper counterpart; the merged multi-pattern program of Sec. 3 is
  * the closest). The non-clique queries share one persistent launch over a device
- * work queue, each with the split thresholds gz_autotune chose for it (if any)
- * and the launch shape tuned for the heaviest tuned query; clique queries take
+ * work queue, each with the split thresholds gz_autotune chose for it (else the
+ * automatic choice described at gz_count_opts, from the query's own width) and
+ * the launch shape tuned for the heaviest tuned query; clique queries take
  * the clique kernels; both kinds overlap on a small per-device stream pool and
  * join `stream` before the call returns.
  * out_counts[nq] (host) receives each query's exact count, identical to gz_count
