@@ -4,15 +4,19 @@
 Default workload (k-clique counting with degree orientation): R-MAT scale 20,
 edge factor 16, (a, b, c, d) = (0.57, 0.19, 0.19, 0.05), seed 20; one step =
 plan K4 and K5 (host planner), orient the device-resident graph (GPU reindex +
-out-list build), count K4 and K5 (GPU enumeration, exact uint64), counts back
-to the host. Metric: intersected elements per second, E / step time, where E is
+out-list build), build the clique rows of the new view (gz_prepare), count K4
+and K5 with one merged program (gz_count_merged: one fused pass over the root
+pairs, exact uint64), counts back to the host. Metric: intersected elements per second, E / step time, where E is
 the number of list elements the bounded linear scans of the paper's nested
 loops consume (computed by the CPU oracle and stored in tests/golden).
 
 Other workloads (--config): triangle (ER 4096, plain method), patterns (R-MAT
-22, five patterns), batched (64 queries over 16 graphs, one launch vs one per
-launch), served (Poisson request stream on a device-resident R-MAT graph, scale
-24 by default, against FIFO one query per launch), motifs, schedules, planner.
+22, five patterns on the oracle's sampled root ranges, one per call and all in
+one batched call), pattern_samples (one range per pattern, for profiling),
+batched (64 queries over 16 graphs, one launch vs one per launch), served
+(Poisson request stream on a device-resident R-MAT graph, scale 24 by default,
+against FIFO one query per launch), motifs (merged vs separate programs),
+schedules, planner.
 The default run also prints short triangle / patterns / batched records
 (--no-subconfigs skips them).
 
